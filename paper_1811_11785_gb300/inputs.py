@@ -1,0 +1,254 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the FP64 oracle.
+
+This module holds no arithmetic of the localisation method itself (no TDOA table,
+no PHAT, no steering matrix, no SVD, no scoring).  It only produces the things the
+method takes as *inputs*:
+
+* the candidate-direction grid (icosphere; SVD-PHAT Section 4 uses 2562 points on a
+  recursively subdivided unit sphere),
+* microphone array geometries (Table 2 of the paper, plus the exact-circle planar
+  variant and random arrays inside a 10 cm sphere),
+* STFT frames of white-noise plane-wave sources with additive white or diffuse noise
+  (the paper's TIMIT / image-method rooms are replaced by this synthetic workload).
+
+Every generator takes an explicit ``numpy.random.Generator`` so a seed fixes the data.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 181111785
+
+# --------------------------------------------------------------------------------------
+# Direction grid
+# --------------------------------------------------------------------------------------
+
+_PHI = (1.0 + 5.0 ** 0.5) / 2.0
+
+_ICO_VERTS = np.array(
+    [
+        [-1, _PHI, 0], [1, _PHI, 0], [-1, -_PHI, 0], [1, -_PHI, 0],
+        [0, -1, _PHI], [0, 1, _PHI], [0, -1, -_PHI], [0, 1, -_PHI],
+        [_PHI, 0, -1], [_PHI, 0, 1], [-_PHI, 0, -1], [-_PHI, 0, 1],
+    ],
+    dtype=np.float64,
+)
+
+_ICO_FACES = [
+    (0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+    (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+    (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+    (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1),
+]
+
+
+def icosphere(level: int) -> np.ndarray:
+    """Unit directions of an icosahedron subdivided ``level`` times: 10*4**level + 2 points.
+
+    Order: the 12 base vertices, then each subdivision appends the (deduplicated) edge
+    midpoints in face-traversal order, projected back onto the unit sphere.  Levels
+    3/4/5/6 give 642/2562/10242/40962 directions.
+    """
+    if level < 0:
+        raise ValueError("level must be >= 0")
+    verts = [v / np.linalg.norm(v) for v in _ICO_VERTS]
+    faces = list(_ICO_FACES)
+    for _ in range(level):
+        mid: dict[tuple[int, int], int] = {}
+
+        def midpoint(a: int, b: int) -> int:
+            key = (a, b) if a < b else (b, a)
+            idx = mid.get(key)
+            if idx is None:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                idx = len(verts) - 1
+                mid[key] = idx
+            return idx
+
+        new_faces = []
+        for (a, b, c) in faces:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            new_faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = new_faces
+    out = np.ascontiguousarray(np.array(verts, dtype=np.float64))
+    assert out.shape[0] == 10 * 4 ** level + 2
+    return out
+
+
+def icosphere_level_for(Q: int) -> int:
+    for lvl in range(0, 9):
+        if 10 * 4 ** lvl + 2 == Q:
+            return lvl
+    raise ValueError(f"Q={Q} is not an icosphere size")
+
+
+# --------------------------------------------------------------------------------------
+# Microphone arrays (metres)
+# --------------------------------------------------------------------------------------
+
+def array_linear_1d() -> np.ndarray:
+    """Table 2, 1-D column: 7 mics on the z axis at -5,-3.3,-1.7,0,1.7,3.3,5 cm."""
+    z = np.array([-5.0, -3.3, -1.7, 0.0, 1.7, 3.3, 5.0]) / 100.0
+    return np.stack([np.zeros(7), np.zeros(7), z], axis=1)
+
+
+def array_planar_2d_table() -> np.ndarray:
+    """Table 2, 2-D column, literal printed coordinates (4.3 cm rather than 5 sin 60)."""
+    xy = [(0, 0), (5, 0), (2.5, 4.3), (-2.5, 4.3), (-5.0, 0), (-2.5, -4.3), (2.5, -4.3)]
+    return np.array([[x / 100.0, y / 100.0, 0.0] for x, y in xy], dtype=np.float64)
+
+
+def array_planar_2d_circle() -> np.ndarray:
+    """Centre mic plus 6 mics on an exact 5 cm circle at 60 degree steps (z = 0)."""
+    pts = [[0.0, 0.0, 0.0]]
+    for i in range(6):
+        a = np.deg2rad(60.0 * i)
+        pts.append([0.05 * np.cos(a), 0.05 * np.sin(a), 0.0])
+    return np.array(pts, dtype=np.float64)
+
+
+def array_3d() -> np.ndarray:
+    """Table 2, 3-D column: centre, then -x,+x,-y,+y,-z,+z at 5 cm."""
+    p = [(0, 0, 0), (-5, 0, 0), (5, 0, 0), (0, -5, 0), (0, 5, 0), (0, 0, -5), (0, 0, 5)]
+    return np.array(p, dtype=np.float64) / 100.0
+
+
+def array_random_ball(rng: np.random.Generator, M: int, radius: float = 0.05,
+                      min_sep: float = 0.01) -> np.ndarray:
+    """M mics drawn uniformly in a ball (rejecting any closer than ``min_sep``)."""
+    pts: list[np.ndarray] = []
+    while len(pts) < M:
+        p = rng.uniform(-radius, radius, size=3)
+        if np.dot(p, p) > radius * radius:
+            continue
+        if all(np.linalg.norm(p - q) >= min_sep for q in pts):
+            pts.append(p)
+    return np.array(pts, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------------------
+# Random directions and STFT frames
+# --------------------------------------------------------------------------------------
+
+def random_directions(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n directions uniform on the unit sphere."""
+    v = rng.standard_normal((n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def hann(N: int) -> np.ndarray:
+    """Periodic Hann window of length N."""
+    n = np.arange(N)
+    return 0.5 - 0.5 * np.cos(2.0 * np.pi * n / N)
+
+
+def _windowed_spectra(rng: np.random.Generator, shape: tuple, N: int, win: np.ndarray):
+    x = rng.standard_normal(shape + (N,))
+    return np.fft.rfft(x * win, axis=-1)
+
+
+def plane_wave_frames(
+    rng: np.random.Generator,
+    mic_xyz: np.ndarray,
+    T: int,
+    N: int,
+    fs: float,
+    c: float,
+    src_dirs: np.ndarray,
+    snr_db: np.ndarray,
+    noise: str = "white",
+    n_diffuse: int = 128,
+    dtype=np.complex64,
+) -> np.ndarray:
+    """STFT frames ``[T][M][N/2+1]`` of white plane-wave sources plus noise.
+
+    ``src_dirs`` is ``(T, S, 3)`` (S simultaneous sources per frame, unit vectors) and
+    ``snr_db`` is ``(T,)``.  Each source is white Gaussian noise, Hann-windowed and
+    transformed with an N-point real FFT; microphone m receives it advanced by
+    ``fs/c * r_m . u`` samples, applied as a phase ramp in frequency
+    (a fractional delay).  Noise is independent white noise per microphone
+    (``noise='white'``) or the sum of ``n_diffuse`` uncorrelated white plane waves
+    from uniformly random directions (``noise='diffuse'``).  SNR is the mic-averaged
+    signal power over noise power of that frame.
+    """
+    mic_xyz = np.asarray(mic_xyz, dtype=np.float64)
+    M = mic_xyz.shape[0]
+    B = N // 2 + 1
+    src_dirs = np.asarray(src_dirs, dtype=np.float64)
+    if src_dirs.ndim == 2:
+        src_dirs = src_dirs[:, None, :]
+    S = src_dirs.shape[1]
+    win = hann(N)
+    k = np.arange(B, dtype=np.float64)
+    out = np.empty((T, M, B), dtype=dtype)
+    chunk = 4096
+    for t0 in range(0, T, chunk):
+        t1 = min(T, t0 + chunk)
+        n = t1 - t0
+        sig = np.zeros((n, M, B), dtype=np.complex128)
+        spec = _windowed_spectra(rng, (n, S), N, win)  # (n, S, B)
+        for s in range(S):
+            d = (fs / c) * (src_dirs[t0:t1, s, :] @ mic_xyz.T)  # (n, M) advance in samples
+            ph = np.exp(2j * np.pi * d[:, :, None] * k[None, None, :] / N)
+            sig += spec[:, s, None, :] * ph
+        if noise == "white":
+            nz = _windowed_spectra(rng, (n, M), N, win)
+        elif noise == "diffuse":
+            nz = np.zeros((n, M, B), dtype=np.complex128)
+            dirs = random_directions(rng, n * n_diffuse).reshape(n, n_diffuse, 3)
+            sp = _windowed_spectra(rng, (n, n_diffuse), N, win)
+            for j in range(n_diffuse):
+                d = (fs / c) * (dirs[:, j, :] @ mic_xyz.T)
+                nz += sp[:, j, None, :] * np.exp(2j * np.pi * d[:, :, None] * k[None, None, :] / N)
+        else:
+            raise ValueError(noise)
+        ps = np.mean(np.abs(sig) ** 2, axis=(1, 2))
+        pn = np.mean(np.abs(nz) ** 2, axis=(1, 2))
+        g = np.sqrt(ps / (pn * 10.0 ** (np.asarray(snr_db[t0:t1], dtype=np.float64) / 10.0)))
+        out[t0:t1] = (sig + g[:, None, None] * nz).astype(dtype)
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Workload presets (the five configurations the build is measured on)
+# --------------------------------------------------------------------------------------
+
+def workload(name: str, T: int | None = None, seed_offset: int = 0):
+    """Return a dict describing a preset workload and its seeded frames.
+
+    Keys: mic_xyz, dirs (grid), fs, c, N, delta, frames [T][M][B] complex64,
+    src_dirs (T,S,3), snr_db (T,).
+    """
+    fs, c = 16000.0, 343.0
+    if name == "linear_q642":           # 7-mic line, Q=642, 100 frames, one direction, 10 dB
+        rng = np.random.default_rng(SEED_BASE + 0 + seed_offset)
+        mic, lvl, N = array_linear_1d(), 3, 512
+        T = 100 if T is None else T
+        u = random_directions(rng, 1)
+        src = np.repeat(u[None, :, :], T, axis=0)
+        snr = np.full(T, 10.0)
+        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "white")
+    elif name == "planar_q2562":        # 7-mic planar circle, Q=2562, SNR U(-5,20)
+        rng = np.random.default_rng(SEED_BASE + 1 + seed_offset)
+        mic, lvl, N = array_planar_2d_circle(), 4, 512
+        T = 65536 if T is None else T
+        src = random_directions(rng, T)[:, None, :]
+        snr = rng.uniform(-5.0, 20.0, size=T)
+        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "white")
+    elif name == "array3d_q10242":      # 7-mic 3-D, Q=10242, 1-2 sources, diffuse noise 0-20 dB
+        rng = np.random.default_rng(SEED_BASE + 3 + seed_offset)
+        mic, lvl, N = array_3d(), 5, 512
+        T = 1 << 20 if T is None else T
+        S = 2
+        src = random_directions(rng, T * S).reshape(T, S, 3)
+        nsrc = rng.integers(1, 3, size=T)
+        # a frame with one source gets its second source at zero amplitude: emulate by
+        # duplicating the first direction (coherent sum keeps a single plane wave).
+        src[nsrc == 1, 1, :] = src[nsrc == 1, 0, :]
+        snr = rng.uniform(0.0, 20.0, size=T)
+        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "diffuse", n_diffuse=32)
+    else:
+        raise ValueError(f"unknown workload {name}")
+    return dict(name=name, mic_xyz=mic, dirs=icosphere(lvl), fs=fs, c=c, N=N, delta=1e-5,
+                frames=frames, src_dirs=src, snr_db=snr)
