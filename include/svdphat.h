@@ -1,0 +1,196 @@
+/*
+ * svdphat.h -- C ABI of the GB300 (sm_103a) SVD-PHAT hot path, libsvdphat.so.
+ *
+ * Method: F. Grondin and J. Glass, "SVD-PHAT: A Fast Sound Source Localization
+ * Method" (arXiv 1811.11785).  Section 2 defines SRP-PHAT (Eq. 1-9), Section 3 the
+ * SVD-PHAT reduction and search (Eq. 10-15) and Algorithm 1 the offline/online split.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Return value: SP_OK (0) or a negative SP_E* code; sp_last_error() then holds a
+ *    one-line message (thread-local).  No C++ exception crosses this boundary.
+ *  - Pointers documented as "device" are CUDA device pointers on the current device;
+ *    "host" pointers are ordinary (ideally pinned) host memory.  The caller owns every
+ *    buffer it passes; the library owns only its opaque handles, which it frees in the
+ *    matching *_destroy call.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).  Work
+ *    is enqueued asynchronously on it unless stated otherwise; device-side failures
+ *    (a bounded wait that gave up) are recorded in a device status word that
+ *    sp_check_status() reads.
+ *  - Microphone pairs p = (i, j), i < j, are numbered in the order of Eq. 7:
+ *    (0,1), (0,2), ..., (M-2, M-1).  B = N/2 + 1 frequency bins k = 0..N/2 and
+ *    L = P * B.  STFT frames are [T][M][B] complex64 (interleaved float re, im).
+ *  - A spectrum entry with |X|^2 < 1e-30 counts as zero; every cross spectrum using it
+ *    is 0 (Eq. 3 divides by magnitudes).  Argmax ties go to the lowest index; a frame
+ *    whose every score is NaN gets index -1.
+ *  - Handles are not thread-safe: calls that use the same handle from several host
+ *    threads, or on several streams at once, must be serialised by the caller
+ *    (a handle owns one device workspace that every localize call on it reuses).
+ */
+#ifndef SVDPHAT_H
+#define SVDPHAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SP_OK        0
+#define SP_EINVAL   (-1)  /* bad argument (size, null pointer, misaligned pointer, ...)   */
+#define SP_ENOMEM   (-2)  /* device or host allocation failed                             */
+#define SP_ECUDA    (-3)  /* a CUDA runtime/driver call failed                            */
+#define SP_ETIMEOUT (-4)  /* a bounded device wait gave up (see sp_check_status)          */
+#define SP_ENOTIMPL (-5)  /* combination of mode / precision / size not supported         */
+
+typedef enum {
+    SP_MODE_SRP = 0,             /* Eq. 9 + Eq. 6: argmax Re{W X} over all Q rows           */
+    SP_MODE_SVD_EXHAUSTIVE = 1,  /* Eq. 12 + Eq. 14: argmax Re{D Z}, Z = V^H X              */
+    SP_MODE_SVD_KDTREE = 2       /* Eq. 15: nearest normalised row D^_q to conj(Z/||Z||)    */
+} sp_mode;
+
+typedef enum {
+    SP_PREC_FP32 = 0,  /* FP32 SIMT arithmetic throughout                                    */
+    SP_PREC_FP16 = 1,  /* FP16 tensor-core projections, FP32 accumulate, FP32 top-8 rescoring */
+    SP_PREC_BF16 = 2   /* BF16 tensor-core projections, FP32 accumulate, FP32 top-8 rescoring */
+} sp_prec;
+
+typedef struct sp_steering sp_steering;  /* TDOA table + steering matrix W (Eq. 2, 4, 8) */
+typedef struct sp_basis sp_basis;        /* rank-K basis V, D = U S, D^, k-d tree (Eq. 10-15) */
+
+/* Thread-local message describing the last failure of this thread (never NULL). */
+const char *sp_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int sp_version(void);
+
+/* ---------------------------------------------------------------------------------
+ * Offline step 1 of Algorithm 1: steering (Eq. 2, Eq. 4, Eq. 8).
+ *
+ * mic_xyz: host, M x 3 doubles (metres), M in [2, 64].
+ * dirs:    host, Q x 3 doubles; candidate directions s_q (need not be unit length,
+ *          Eq. 2 divides by ||s_q||; a zero vector is SP_EINVAL).  Q in [1, 2^24].
+ * fs, c:   sample rate (Hz) and speed of sound (m/s), both > 0.
+ * N:       STFT frame size, even, in [4, 8192].
+ * flags:   bit 0 (SP_STEER_MATERIALIZE_W): also materialise W (Q x L complex64 on the
+ *          device) for SP_MODE_SRP.  Without it SRP localisation is SP_ENOTIMPL.
+ * out:     receives the new handle.
+ *
+ * The TDOA table tau[q][p] = fs/c * (r_j - r_i) . s_q/||s_q|| is computed on the device
+ * in FP64 with the fixed operation order n = sqrt((sx*sx + sy*sy) + sz*sz),
+ * u = s / n, tau = (fs/c) * ((dx*ux + dy*uy) + dz*uz), every step correctly rounded.
+ * W[q][p*B + k] = exp(2 pi i k tau[q][p] / N), phase reduced in FP64.
+ * Synchronous (returns when the table is built).
+ * --------------------------------------------------------------------------------- */
+#define SP_STEER_MATERIALIZE_W 1
+int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q,
+                      double fs, double c, int N, int flags, sp_steering **out);
+
+/* Dimensions of a steering handle; any pointer may be NULL. */
+int sp_steering_dims(const sp_steering *st, int *M, int *P, int *Q, int *N, int *B);
+
+/* Copy the FP64 TDOA table (Q x P, row-major) to host memory. Synchronous. */
+int sp_steering_tau(const sp_steering *st, double *tau_host);
+
+/* Copy W (Q x L complex64, row-major, column p*B + k as in Eq. 8) into a device buffer.
+ * SP_EINVAL if W was not materialised. Asynchronous on stream. */
+int sp_steering_w(const sp_steering *st, void *w_dev, void *stream);
+
+void sp_steering_destroy(sp_steering *st);
+
+/* ---------------------------------------------------------------------------------
+ * Offline steps 2-4 of Algorithm 1 (Eq. 10-13, Section 3).
+ *
+ * Truncated SVD W ~= U S V^H by randomized block subspace iteration in FP64 on the
+ * device (products with W generated from the TDOA table) and a Rayleigh-Ritz step on
+ * the host.  K is the smallest rank with sum_{k<=K} s_k^2 >= (1 - delta) Tr{W W^H}
+ * (Eq. 11, Tr{W W^H} = Q L); if that K splits a cluster of equal singular values
+ * (s_{K+1}^2 >= s_K^2 - 1e-10 s_1^2) it is extended to the end of the cluster.
+ * D = U S = W V (Eq. 13) is formed in FP64, D^_q = D_q / ||D_q||, and a k-d tree over
+ * the real 2K-dimensional rows [Re D^_q, Im D^_q] is built on the host and uploaded.
+ *
+ * delta in (0, 1).  flags: reserved, pass 0.  K_out (may be NULL) receives K.
+ * The steering handle must outlive the basis.  Synchronous.
+ * --------------------------------------------------------------------------------- */
+int sp_svd_reduce(const sp_steering *st, double delta, int flags, sp_basis **out, int *K_out);
+
+/* K, the number of computed Ritz values n_sigma, and (if sigma2_host != NULL) the
+ * first min(n_sigma, cap) squared singular values in descending order. */
+int sp_basis_info(const sp_basis *b, int *K, int *n_sigma, double *sigma2_host, int cap);
+
+/* Copy V (L x K complex128, row-major, interleaved re/im) or D (Q x K complex128) to host. */
+int sp_basis_v(const sp_basis *b, double *v_host);
+int sp_basis_d(const sp_basis *b, double *d_host);
+
+/* k-d tree shape: number of nodes, leaf bucket size and depth. */
+int sp_basis_kdtree_info(const sp_basis *b, int *n_nodes, int *leaf_size, int *depth);
+
+void sp_basis_destroy(sp_basis *b);
+
+/* ---------------------------------------------------------------------------------
+ * Online step 1 (Eq. 3, Eq. 7) on its own: PHAT cross spectra of all pairs.
+ * frames_dev: device [T][M][B] complex64 (8-byte aligned).  x_dev: device [T][L]
+ * complex64, column p*B + k.  T >= 0 (T = 0 is a no-op).
+ * --------------------------------------------------------------------------------- */
+int sp_phat(const void *frames_dev, int T, int M, int B, void *x_dev, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Online steps 1-2 (Eq. 3, 7, 12): Z = V^H X for every frame, PHAT fused.
+ * z_dev: device [T][K] complex64.  prec selects FP32 SIMT or the FP16/BF16 tensor-core
+ * GEMM (FP32 accumulate).
+ * --------------------------------------------------------------------------------- */
+int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
+               void *z_dev, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * The online hot path (Algorithm 1, online steps 1-4) for T frames.
+ *
+ * mode SP_MODE_SRP:            idx = argmax_q Re{W_q X} (needs a materialised W; prec
+ *                              must be SP_PREC_FP32).
+ * mode SP_MODE_SVD_EXHAUSTIVE: idx = argmax_q Re{D_q Z} (Eq. 14).  With FP16/BF16 the
+ *                              scan keeps each frame's 8 best candidates and rescores
+ *                              them in FP32 against FP32 Z and D.
+ * mode SP_MODE_SVD_KDTREE:     idx = nearest D^_q to conj(Z/||Z||) by exact k-d tree
+ *                              search (Eq. 15), FP32 distances.
+ *
+ * idx_dev:        device int32 [T], required.
+ * score_dev:      device float [T] or NULL: Y_idx = Re{W_idx X}, the SRP-PHAT energy of
+ *                 the chosen direction from its regenerated row of W (Algorithm 1,
+ *                 online step 4).  NULL skips step 4.
+ * proj_score_dev: device float [T] or NULL: the search's own score, Re{D_idx Z} for the
+ *                 SVD modes (Re{D^_idx Z^} for the k-d tree), Re{W_idx X} for SRP.
+ * Asynchronous on stream; the basis workspace is reused by the next call.
+ * --------------------------------------------------------------------------------- */
+int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec,
+                int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream);
+
+/* Plain SRP-PHAT (Eq. 5, 6, 9) straight from a steering handle (no basis needed). */
+int sp_localize_srp(const sp_steering *st, const void *frames_dev, int T,
+                    int32_t *idx_dev, float *score_dev, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * sp_localize from HOST buffers: frames_host [T][M][B] complex64, idx_host int32 [T],
+ * score_host / proj_score_host float [T] or NULL.  Frames are copied in chunks of
+ * chunk_frames (0 = library default) through two device staging buffers so that the
+ * host-to-device copy of chunk c+1 overlaps the localisation of chunk c.  Pinned host
+ * memory is needed for the copies to be asynchronous.  Returns when every result is
+ * in host memory.
+ * --------------------------------------------------------------------------------- */
+int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode mode,
+                     sp_prec prec, int32_t *idx_host, float *score_host,
+                     float *proj_score_host, int chunk_frames, void *stream);
+
+/* Synchronise stream and report a device-side failure recorded since the last call
+ * (SP_ETIMEOUT if a bounded wait gave up), clearing it. */
+int sp_check_status(void *stream);
+
+/* For tests: set the iteration budget of every bounded device wait (0 = default).
+ * A budget of 1 makes waits give up at once, which exercises SP_ETIMEOUT. */
+int sp_set_wait_budget(long long iterations);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVDPHAT_H */

@@ -1,0 +1,283 @@
+"""Thin Python binding of libsvdphat.so (``include/svdphat.h``): argument marshalling only.
+
+Every step of the localisation path runs in the library's CUDA kernels; PyTorch only
+provides device memory and the current CUDA stream.  There is no fallback: if the shared
+library has not been built (``paper_1811_11785_gb300.build.build()``) or there is no GPU,
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MODE = {"srp": 0, "svd_exhaustive": 1, "svd_kdtree": 2}
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+STEER_MATERIALIZE_W = 1
+
+SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_ETIMEOUT, SP_ENOTIMPL = 0, -1, -2, -3, -4, -5
+
+
+class SvdPhatError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed with code {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "sp_last_error": ([], ctypes.c_char_p),
+    "sp_version": ([], ctypes.c_int),
+    "sp_build_steering": ([_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+    "sp_steering_dims": ([_vp, _ip, _ip, _ip, _ip, _ip], ctypes.c_int),
+    "sp_steering_tau": ([_vp, _dp], ctypes.c_int),
+    "sp_steering_w": ([_vp, _vp, _vp], ctypes.c_int),
+    "sp_steering_destroy": ([_vp], None),
+    "sp_svd_reduce": ([_vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp), _ip], ctypes.c_int),
+    "sp_basis_info": ([_vp, _ip, _ip, _dp, ctypes.c_int], ctypes.c_int),
+    "sp_basis_v": ([_vp, _dp], ctypes.c_int),
+    "sp_basis_d": ([_vp, _dp], ctypes.c_int),
+    "sp_basis_kdtree_info": ([_vp, _ip, _ip, _ip], ctypes.c_int),
+    "sp_basis_destroy": ([_vp], None),
+    "sp_phat": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "sp_project": ([_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "sp_localize": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "sp_localize_srp": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "sp_localize_host": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
+                          _vp], ctypes.c_int),
+    "sp_check_status": ([_vp], ctypes.c_int),
+    "sp_set_wait_budget": ([ctypes.c_longlong], ctypes.c_int),
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def lib():
+    """Load libsvdphat.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; call paper_1811_11785_gb300.build.build() first")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(fn: str, rc: int):
+    if rc != SP_OK:
+        raise SvdPhatError(fn, rc, lib().sp_last_error().decode())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _mode(m):
+    return MODE[m] if isinstance(m, str) else int(m)
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _frames(frames, st):
+    import torch
+    if not (isinstance(frames, torch.Tensor) and frames.is_cuda and frames.dtype == torch.complex64):
+        raise TypeError("frames must be a CUDA complex64 tensor [T][M][N/2+1]")
+    if not frames.is_contiguous():
+        raise ValueError("frames must be contiguous")
+    if frames.dim() != 3 or (st is not None and (frames.shape[1] != st.M or frames.shape[2] != st.B)):
+        raise ValueError("frames must have shape [T][M][N/2+1] matching the steering handle")
+    return frames
+
+
+class Steering:
+    """TDOA table and steering matrix W (Eq. 2, 4, 8) on the device."""
+
+    def __init__(self, mic_xyz, dirs, fs: float, c: float, N: int, materialize_w: bool = False):
+        L = lib()
+        mic = np.ascontiguousarray(mic_xyz, dtype=np.float64)
+        d = np.ascontiguousarray(dirs, dtype=np.float64)
+        h = _vp()
+        _check("sp_build_steering",
+               L.sp_build_steering(mic.ctypes.data_as(_dp), mic.shape[0], d.ctypes.data_as(_dp), d.shape[0],
+                                   float(fs), float(c), int(N),
+                                   STEER_MATERIALIZE_W if materialize_w else 0, ctypes.byref(h)))
+        self._h = h
+        v = [ctypes.c_int() for _ in range(5)]
+        _check("sp_steering_dims", L.sp_steering_dims(h, *[ctypes.byref(x) for x in v]))
+        self.M, self.P, self.Q, self.N, self.B = (x.value for x in v)
+        self.L = self.P * self.B
+        self.materialized = materialize_w
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tau(self) -> np.ndarray:
+        out = np.empty((self.Q, self.P), dtype=np.float64)
+        _check("sp_steering_tau", lib().sp_steering_tau(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def w(self):
+        import torch
+        out = torch.empty((self.Q, self.L), dtype=torch.complex64, device="cuda")
+        _check("sp_steering_w", lib().sp_steering_w(self._h, _ptr(out), _stream()))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sp_steering_destroy(h)
+            self._h = None
+
+
+class Basis:
+    """Rank-K basis (V, D = U S, D^) and k-d tree from Eq. 10-15; keeps its Steering alive."""
+
+    def __init__(self, steering: Steering, delta: float):
+        L = lib()
+        h = _vp()
+        K = ctypes.c_int()
+        _check("sp_svd_reduce", L.sp_svd_reduce(steering.handle, float(delta), 0, ctypes.byref(h), ctypes.byref(K)))
+        self._h = h
+        self.steering = steering
+        self.K = K.value
+        self.delta = delta
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sigma2(self) -> np.ndarray:
+        n = ctypes.c_int()
+        _check("sp_basis_info", lib().sp_basis_info(self._h, None, ctypes.byref(n), None, 0))
+        out = np.empty(n.value)
+        _check("sp_basis_info", lib().sp_basis_info(self._h, None, None, out.ctypes.data_as(_dp), n.value))
+        return out
+
+    def V(self) -> np.ndarray:
+        out = np.empty((self.steering.L, self.K), dtype=np.complex128)
+        _check("sp_basis_v", lib().sp_basis_v(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def D(self) -> np.ndarray:
+        out = np.empty((self.steering.Q, self.K), dtype=np.complex128)
+        _check("sp_basis_d", lib().sp_basis_d(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def kdtree_info(self) -> dict:
+        v = [ctypes.c_int() for _ in range(3)]
+        _check("sp_basis_kdtree_info", lib().sp_basis_kdtree_info(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(n_nodes=v[0].value, leaf_size=v[1].value, depth=v[2].value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sp_basis_destroy(h)
+            self._h = None
+
+
+def build_steering(mic_xyz, dirs, fs, c, N, materialize_w=False) -> Steering:
+    return Steering(mic_xyz, dirs, fs, c, N, materialize_w)
+
+
+def svd_reduce(steering: Steering, delta: float) -> Basis:
+    return Basis(steering, delta)
+
+
+def phat(frames):
+    """Eq. 3 / Eq. 7 for every frame: complex64 [T][P*B]."""
+    import torch
+    _frames(frames, None)
+    T, M, B = frames.shape
+    X = torch.empty((T, M * (M - 1) // 2 * B), dtype=torch.complex64, device=frames.device)
+    _check("sp_phat", lib().sp_phat(_ptr(frames), T, M, B, _ptr(X), _stream()))
+    return X
+
+
+def project(basis: Basis, frames, prec="fp16"):
+    """Eq. 12 with fused PHAT: Z = V^H X, complex64 [T][K]."""
+    import torch
+    _frames(frames, basis.steering)
+    Z = torch.empty((frames.shape[0], basis.K), dtype=torch.complex64, device=frames.device)
+    _check("sp_project", lib().sp_project(basis.handle, _ptr(frames), frames.shape[0], _prec(prec), _ptr(Z),
+                                          _stream()))
+    return Z
+
+
+def localize(basis: Basis, frames, mode="svd_exhaustive", prec="fp16", score=True, proj=True, out=None):
+    """Algorithm 1 online steps 1-4.  Returns (idx int32, score float32 | None, proj float32 | None)."""
+    import torch
+    _frames(frames, basis.steering)
+    T = frames.shape[0]
+    if out is None:
+        idx = torch.empty(T, dtype=torch.int32, device=frames.device)
+        sc = torch.empty(T, dtype=torch.float32, device=frames.device) if score else None
+        pj = torch.empty(T, dtype=torch.float32, device=frames.device) if proj else None
+    else:
+        idx, sc, pj = out
+    _check("sp_localize", lib().sp_localize(basis.handle, _ptr(frames), T, _mode(mode), _prec(prec), _ptr(idx),
+                                            _ptr(sc), _ptr(pj), _stream()))
+    return idx, sc, pj
+
+
+def localize_srp(steering: Steering, frames, score=True):
+    """Plain SRP-PHAT (Eq. 5, 6, 9): argmax Re{W X} in FP32; returns (idx, best score)."""
+    import torch
+    _frames(frames, steering)
+    T = frames.shape[0]
+    idx = torch.empty(T, dtype=torch.int32, device=frames.device)
+    sc = torch.empty(T, dtype=torch.float32, device=frames.device) if score else None
+    _check("sp_localize_srp", lib().sp_localize_srp(steering.handle, _ptr(frames), T, _ptr(idx), _ptr(sc),
+                                                    _stream()))
+    return idx, sc
+
+
+def localize_host(basis: Basis, frames_host, mode="svd_exhaustive", prec="fp16", score=True, proj=True,
+                  chunk_frames=0, out=None):
+    """sp_localize from host buffers (pinned CPU tensors); returns CPU tensors."""
+    import torch
+    if frames_host.is_cuda or frames_host.dtype != torch.complex64 or not frames_host.is_contiguous():
+        raise TypeError("frames_host must be a contiguous CPU complex64 tensor")
+    T = frames_host.shape[0]
+    if out is None:
+        pin = frames_host.is_pinned()
+        idx = torch.empty(T, dtype=torch.int32, pin_memory=pin)
+        sc = torch.empty(T, dtype=torch.float32, pin_memory=pin) if score else None
+        pj = torch.empty(T, dtype=torch.float32, pin_memory=pin) if proj else None
+    else:
+        idx, sc, pj = out
+    _check("sp_localize_host", lib().sp_localize_host(basis.handle, _ptr(frames_host), T, _mode(mode), _prec(prec),
+                                                      _ptr(idx), _ptr(sc), _ptr(pj), int(chunk_frames),
+                                                      _stream()))
+    return idx, sc, pj
+
+
+def check_status():
+    _check("sp_check_status", lib().sp_check_status(_stream()))
+
+
+def set_wait_budget(cycles: int):
+    _check("sp_set_wait_budget", lib().sp_set_wait_budget(int(cycles)))

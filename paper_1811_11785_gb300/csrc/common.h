@@ -1,0 +1,167 @@
+// Internal declarations shared by the translation units of libsvdphat.so.
+// Host-side only (no device code); kernels live in the .cu files and are reached
+// through the launch_* functions declared here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/svdphat.h"
+
+namespace sp {
+
+// ---------------------------------------------------------------- error plumbing
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define SP_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::sp::fail(SP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define SP_CHECK(cond, code, msg)                                                       \
+    do {                                                                                \
+        if (!(cond)) return ::sp::fail((code), (msg));                                  \
+    } while (0)
+
+#define SP_TRY(call)                                                                    \
+    do {                                                                                \
+        int r_ = (call);                                                                \
+        if (r_ != SP_OK) return r_;                                                     \
+    } while (0)
+
+// ---------------------------------------------------------------- device buffers
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    int reserve(size_t n);
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------- device status word
+// Set by kernels whose bounded waits gave up (see sp_check_status).
+int read_and_clear_device_status(cudaStream_t s, int *status);
+long long wait_budget();
+
+// ---------------------------------------------------------------- tiling of the
+// tensor-core projection (K-dimension layout of GEMM1, chosen for the GPU; the paper's
+// Eq. 7 column order p*B + k is a different permutation of the same contraction index).
+//   chunk c covers bins 4c .. 4c+3; inside a chunk, pair p and bin b sit at element
+//   p*8 + 2b (+0 real, +1 imaginary); a chunk spans kAtomsPerChunk 64-element atoms.
+constexpr int kChunkBins = 4;
+struct TcLayout {
+    int P = 0, Pp = 0;            // pairs and pairs rounded up to even
+    int steps_per_chunk = 0;      // K16 MMA steps per chunk = Pp / 2
+    int atoms_per_chunk = 0;      // 64-element swizzle atoms per chunk
+    int n_chunks = 0;             // ceil(B / 4)
+    int row_elems = 0;            // n_chunks * atoms_per_chunk * 64
+    int n1 = 0;                   // GEMM1 N = 2K rounded up to a multiple of 16
+    int k2 = 0;                   // GEMM2 K = 2K rounded up to 16
+    int k2_atoms = 0;             // 64-element atoms of the GEMM2 K dimension
+    int n2 = 128;                 // Q tile of GEMM2
+};
+TcLayout make_tc_layout(int P, int B, int K);
+
+// ---------------------------------------------------------------- k-d tree
+struct KdNode {               // 16 bytes
+    int32_t dim;              // split dimension, or -1 for a leaf
+    float split;              // split value (points with x[dim] < split go left)
+    int32_t right;            // index of the right child (left child is this + 1); leaf: first slot
+    int32_t count;            // leaf: number of points in the bucket (0 for internal nodes)
+};
+
+// ---------------------------------------------------------------- handles
+}  // namespace sp
+
+struct sp_basis;
+namespace sp {
+void tc_release(sp_basis *b);  // frees the tensor maps of the tensor-core path
+}
+
+struct sp_steering {
+    int device = 0;
+    int M = 0, P = 0, Q = 0, N = 0, B = 0, L = 0;
+    double fs = 0, c = 0;
+    std::vector<double> mic, dirs;      // host copies (M x 3, Q x 3)
+    std::vector<int> pair_i, pair_j;    // Eq. 7 pair order
+    std::vector<double> tau_host;       // Q x P
+    sp::DevBuf tau;                     // Q x P double
+    sp::DevBuf d_mic;                   // M x 3 double
+    sp::DevBuf d_dirs;                  // Q x 3 double (unit directions, for step 4)
+    sp::DevBuf W;                       // Q x L complex64 (optional)
+    bool has_w = false;
+    mutable sp::DevBuf work;            // workspace for SRP calls on this handle
+};
+
+struct sp_basis {
+    const sp_steering *st = nullptr;
+    int K = 0;
+    double delta = 0;
+    std::vector<double> sigma2;         // Ritz values, descending
+    std::vector<double> V, D;           // host FP64 complex, L x K and Q x K (interleaved)
+    // device copies
+    sp::DevBuf Vc32;                    // V^T as complex64 [K][L], column l = p*B + k (Eq. 7 order)
+    sp::DevBuf Dc32;                    // D as complex64 [Q][K]
+    sp::TcLayout tc;
+    sp::DevBuf Vtc[2];                  // GEMM1 B operand, fp16 [0] / bf16 [1]: [n1][row_elems]
+    sp::DevBuf Dtc[2];                  // GEMM2 B operand, fp16 / bf16: [Q][k2_atoms*64]
+    float v_scale = 1.f;                // Vtc holds V * v_scale
+    void *tc_maps = nullptr;            // TMA descriptors of Vtc / Dtc (owned)
+    // k-d tree over the rows [Re D^_q, Im D^_q]
+    std::vector<sp::KdNode> nodes_host;
+    sp::DevBuf nodes;                   // KdNode[n_nodes]
+    sp::DevBuf leaf_pts;                // float [n_slots/32][2K][32] bucket-major, dimension-major
+    sp::DevBuf leaf_ids;                // int32 [n_slots]
+    int n_nodes = 0, leaf_size = 32, depth = 0, n_slots = 0;
+    mutable sp::DevBuf work;            // workspace for localize calls
+    mutable sp::DevBuf stage[2];        // host-path staging
+    mutable cudaStream_t copy_stream = nullptr;      // host-path copies
+    mutable cudaEvent_t ev_loaded[2] = {nullptr, nullptr};
+    mutable cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    ~sp_basis() {
+        sp::tc_release(this);
+        for (int i = 0; i < 2; ++i) {
+            if (ev_loaded[i]) cudaEventDestroy(ev_loaded[i]);
+            if (ev_free[i]) cudaEventDestroy(ev_free[i]);
+        }
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+    }
+};
+
+namespace sp {
+// launchers implemented in the .cu files ------------------------------------------
+int launch_tau(const sp_steering *st, cudaStream_t s);
+int launch_w(const sp_steering *st, cudaStream_t s);
+int launch_phat(const void *frames, int T, int M, int B, void *x, cudaStream_t s);
+// Y = Re{A_q . X_t} over contraction length Lc (A: [Qa][Lc] complex64, X: [T][Lc] complex64),
+// argmax over q per frame -> idx / best (keys scratch: T x uint64).
+int launch_srp_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint64_t *keys,
+                      int32_t *idx, float *best, cudaStream_t s);
+int launch_project_f32(const sp_basis *b, const void *X, int T, void *Z, cudaStream_t s);
+int launch_svd_scan_f32(const sp_basis *b, const void *Z, int T, uint64_t *keys, int32_t *idx,
+                        float *best, cudaStream_t s);
+int launch_score_row(const sp_steering *st, const void *frames, int T, const int32_t *idx,
+                     float *score, cudaStream_t s);
+int launch_svd_tc(const sp_basis *b, const void *frames, int T, int prec, int32_t *idx,
+                  float *proj, void *z_out, cudaStream_t s);
+int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
+                  cudaStream_t s);
+int tc_prepare(sp_basis *b);   // upload GEMM1/GEMM2 operands in the tensor-core layouts
+int reduce_basis(const sp_steering *st, double delta, sp_basis *b);
+int build_kdtree(sp_basis *b);
+}  // namespace sp

@@ -1,0 +1,241 @@
+// Offline step 4 and online step 3 of Algorithm 1: a k-d tree (Bentley 1975) over the
+// normalised rows D^_q = D_q / ||D_q|| and its exact nearest-neighbour search (Eq. 15).
+//
+// Eq. 15: Re{D^_q Z^} = 1 - ||D^_q - conj(Z^)||^2 / 2 for unit vectors, so the direction
+// maximising the normalised score is the nearest neighbour of conj(Z^) among the D^_q,
+// searched in the real 2K-dimensional embedding x_q = [Re D^_q, Im D^_q] with query
+// [Re Z^, -Im Z^].
+//
+// Build (host): split on the dimension of largest spread at the median (ties broken by
+// index), recursively, until a node holds at most 32 points (one leaf bucket = one warp).
+// Search (device): one warp per query; the warp walks the tree with an explicit stack,
+// visiting the near child first and keeping the far child only if the squared distance
+// from the query to the splitting plane does not exceed the best distance so far
+// (exact search).  A leaf's 32 points are stored dimension-major so that lane j reads
+// point j coalesced; lanes then reduce (distance, index) to the lexicographic minimum.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.h"
+
+namespace sp {
+
+constexpr int kLeaf = 32;
+constexpr int kMaxDepth = 64;
+constexpr int kMaxDims = 512;
+
+namespace {
+struct Builder {
+    int dim = 0;
+    const std::vector<float> *pts = nullptr;   // Q x dim
+    std::vector<KdNode> nodes;
+    std::vector<int> bucket_ids;                // n_buckets x 32 (-1 = empty slot)
+    int depth = 0;
+
+    float x(int id, int d) const { return (*pts)[(size_t)id * dim + d]; }
+
+    int build(std::vector<int> &ids, int lo, int hi, int level) {
+        depth = std::max(depth, level + 1);
+        const int me = (int)nodes.size();
+        nodes.push_back(KdNode{-1, 0.f, 0, 0});
+        if (hi - lo <= kLeaf) {
+            const int bucket = (int)(bucket_ids.size() / kLeaf);
+            for (int i = 0; i < kLeaf; ++i) bucket_ids.push_back(lo + i < hi ? ids[lo + i] : -1);
+            nodes[me] = KdNode{-1, 0.f, bucket, hi - lo};
+            return me;
+        }
+        int best_d = 0;
+        float best_spread = -1.f;
+        for (int d = 0; d < dim; ++d) {
+            float mn = x(ids[lo], d), mx = mn;
+            for (int i = lo + 1; i < hi; ++i) {
+                const float v = x(ids[i], d);
+                mn = std::min(mn, v);
+                mx = std::max(mx, v);
+            }
+            if (mx - mn > best_spread) {
+                best_spread = mx - mn;
+                best_d = d;
+            }
+        }
+        std::sort(ids.begin() + lo, ids.begin() + hi, [&](int a, int b) {
+            const float va = x(a, best_d), vb = x(b, best_d);
+            return va < vb || (va == vb && a < b);
+        });
+        const int mid = (lo + hi) / 2;
+        const float split = x(ids[mid], best_d);  // left: x <= split, right: x >= split
+        build(ids, lo, mid, level + 1);
+        const int right = build(ids, mid, hi, level + 1);
+        nodes[me] = KdNode{best_d, split, right, 0};
+        return me;
+    }
+};
+}  // namespace
+
+int build_kdtree(sp_basis *b) {
+    const int Q = b->st->Q, K = b->K, dim = 2 * K;
+    SP_CHECK(dim <= kMaxDims, SP_ENOTIMPL, "k-d tree supports 2K <= 512");
+    std::vector<float> pts((size_t)Q * dim);
+    for (int q = 0; q < Q; ++q) {
+        double n2 = 0;
+        for (int k = 0; k < K; ++k) {
+            const double re = b->D[((size_t)q * K + k) * 2], im = b->D[((size_t)q * K + k) * 2 + 1];
+            n2 += re * re + im * im;
+        }
+        const double inv = n2 > 0 ? 1.0 / std::sqrt(n2) : 0.0;
+        for (int k = 0; k < K; ++k) {
+            pts[(size_t)q * dim + k] = (float)(b->D[((size_t)q * K + k) * 2] * inv);
+            pts[(size_t)q * dim + K + k] = (float)(b->D[((size_t)q * K + k) * 2 + 1] * inv);
+        }
+    }
+    Builder bd;
+    bd.dim = dim;
+    bd.pts = &pts;
+    std::vector<int> ids(Q);
+    std::iota(ids.begin(), ids.end(), 0);
+    bd.build(ids, 0, Q, 0);
+    SP_CHECK(bd.depth <= kMaxDepth, SP_ENOTIMPL, "k-d tree too deep");
+    const int nb = (int)(bd.bucket_ids.size() / kLeaf);
+    std::vector<float> leaf((size_t)nb * dim * kLeaf, 1e18f);
+    for (int bkt = 0; bkt < nb; ++bkt)
+        for (int j = 0; j < kLeaf; ++j) {
+            const int id = bd.bucket_ids[(size_t)bkt * kLeaf + j];
+            if (id < 0) continue;
+            for (int d = 0; d < dim; ++d)
+                leaf[((size_t)bkt * dim + d) * kLeaf + j] = pts[(size_t)id * dim + d];
+        }
+    b->nodes_host = bd.nodes;
+    b->n_nodes = (int)bd.nodes.size();
+    b->depth = bd.depth;
+    b->leaf_size = kLeaf;
+    b->n_slots = nb * kLeaf;
+    SP_TRY(b->nodes.reserve(bd.nodes.size() * sizeof(KdNode)));
+    SP_TRY(b->leaf_pts.reserve(leaf.size() * 4));
+    SP_TRY(b->leaf_ids.reserve(bd.bucket_ids.size() * 4));
+    SP_CUDA(cudaMemcpy(b->nodes.p, bd.nodes.data(), bd.nodes.size() * sizeof(KdNode), cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMemcpy(b->leaf_pts.p, leaf.data(), leaf.size() * 4, cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMemcpy(b->leaf_ids.p, bd.bucket_ids.data(), bd.bucket_ids.size() * 4, cudaMemcpyHostToDevice));
+    return SP_OK;
+}
+
+// One warp per query.  Shared memory per warp: the query (2K floats) and the stack.
+constexpr int KD_WARPS = 4;
+
+__global__ void __launch_bounds__(KD_WARPS * 32)
+    kdtree_kernel(const float2 *__restrict__ Z, int T, int K, const KdNode *__restrict__ nodes,
+                  const float *__restrict__ leaf_pts, const int32_t *__restrict__ leaf_ids,
+                  int32_t *__restrict__ idx_out, float *__restrict__ proj_out) {
+    extern __shared__ float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dim = 2 * K;
+    float *qv = smem + warp * dim;
+    int *stk_node = reinterpret_cast<int *>(smem + KD_WARPS * dim) + warp * kMaxDepth;
+    float *stk_bound = reinterpret_cast<float *>(smem + KD_WARPS * dim + KD_WARPS * kMaxDepth) +
+                       warp * kMaxDepth;
+    const long long t = (long long)blockIdx.x * KD_WARPS + warp;
+    if (t >= T) return;
+    // query: conj(Z / ||Z||) embedded as [Re, -Im]
+    float n2 = 0.f;
+    for (int k = lane; k < K; k += 32) {
+        const float2 z = Z[(size_t)t * K + k];
+        n2 += z.x * z.x + z.y * z.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    if (!(n2 > 0.f) || !isfinite(n2)) {
+        if (lane == 0) {
+            idx_out[t] = -1;
+            if (proj_out) proj_out[t] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    const float inv = rsqrtf(n2);
+    for (int k = lane; k < K; k += 32) {
+        const float2 z = Z[(size_t)t * K + k];
+        qv[k] = z.x * inv;
+        qv[K + k] = -z.y * inv;
+    }
+    __syncwarp();
+    float best_d = __int_as_float(0x7f800000);
+    int best_id = 0x7fffffff;
+    int sp = 0;
+    if (lane == 0) {
+        stk_node[0] = 0;
+        stk_bound[0] = 0.f;
+    }
+    sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+        --sp;
+        int node = stk_node[sp];
+        float bound = stk_bound[sp];
+        __syncwarp();
+        if (bound > best_d) continue;
+        KdNode nd = nodes[node];
+        while (nd.dim >= 0) {
+            const float diff = qv[nd.dim] - nd.split;
+            const int near_c = diff < 0.f ? node + 1 : nd.right;
+            const int far_c = diff < 0.f ? nd.right : node + 1;
+            const float fb = fmaxf(bound, diff * diff);
+            if (fb <= best_d && sp < kMaxDepth) {
+                if (lane == 0) {
+                    stk_node[sp] = far_c;
+                    stk_bound[sp] = fb;
+                }
+                ++sp;
+            }
+            node = near_c;
+            nd = nodes[node];
+        }
+        __syncwarp();
+        // leaf bucket: lane j scores point j
+        const int bucket = nd.right;
+        const float *pb = leaf_pts + (size_t)bucket * dim * 32 + lane;
+        float d2 = 0.f;
+        for (int d = 0; d < dim; ++d) {
+            const float df = qv[d] - pb[(size_t)d * 32];
+            d2 = fmaf(df, df, d2);
+        }
+        int id = leaf_ids[(size_t)bucket * 32 + lane];
+        if (id < 0) {
+            d2 = __int_as_float(0x7f800000);
+            id = 0x7fffffff;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, d2, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, id, o);
+            if (od < d2 || (od == d2 && oi < id)) {
+                d2 = od;
+                id = oi;
+            }
+        }
+        if (d2 < best_d || (d2 == best_d && id < best_id)) {
+            best_d = d2;
+            best_id = id;
+        }
+    }
+    if (lane == 0) {
+        idx_out[t] = best_id == 0x7fffffff ? -1 : best_id;
+        if (proj_out) proj_out[t] = 1.f - 0.5f * best_d;
+    }
+}
+
+int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
+                  cudaStream_t s) {
+    if (T == 0) return SP_OK;
+    const int dim = 2 * b->K;
+    const size_t smem = (size_t)KD_WARPS * dim * 4 + (size_t)KD_WARPS * kMaxDepth * 8;
+    const long long blocks = ((long long)T + KD_WARPS - 1) / KD_WARPS;
+    kdtree_kernel<<<(unsigned)blocks, KD_WARPS * 32, smem, s>>>(
+        (const float2 *)Z, T, b->K, b->nodes.as<KdNode>(), b->leaf_pts.as<float>(),
+        b->leaf_ids.as<int32_t>(), idx, proj);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+}  // namespace sp

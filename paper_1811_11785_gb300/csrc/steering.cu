@@ -1,0 +1,87 @@
+// Offline step 1 of Algorithm 1: the far-field TDOA table (Eq. 2) and the steering
+// matrix W (Eq. 4, stacked as Eq. 8).
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace sp {
+
+// tau[q][p] = fs/c * (r_j - r_i) . s_q / ||s_q||  (Eq. 2), one thread per (q, p).
+// Fixed order, every operation correctly rounded and never contracted into an FMA:
+//   n = sqrt((sx*sx + sy*sy) + sz*sz), u = s / n,
+//   tau = (fs / c) * ((dx*ux + dy*uy) + dz*uz), d = r_j - r_i.
+// The same order on any IEEE-754 machine gives the same bits.
+__global__ void tau_kernel(const double *__restrict__ mic, const double *__restrict__ dirs,
+                           const int *__restrict__ pi, const int *__restrict__ pj, int Q, int P,
+                           double fs, double c, double *__restrict__ tau, double *__restrict__ unit) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Q * P) return;
+    const int q = (int)(idx / P), p = (int)(idx % P);
+    const double sx = dirs[3 * q], sy = dirs[3 * q + 1], sz = dirs[3 * q + 2];
+    const double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)),
+                                          __dmul_rn(sz, sz)));
+    const double ux = __ddiv_rn(sx, n), uy = __ddiv_rn(sy, n), uz = __ddiv_rn(sz, n);
+    const int i = pi[p], j = pj[p];
+    const double dx = __dsub_rn(mic[3 * j], mic[3 * i]);
+    const double dy = __dsub_rn(mic[3 * j + 1], mic[3 * i + 1]);
+    const double dz = __dsub_rn(mic[3 * j + 2], mic[3 * i + 2]);
+    const double g = __ddiv_rn(fs, c);
+    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(dx, ux), __dmul_rn(dy, uy)), __dmul_rn(dz, uz));
+    tau[idx] = __dmul_rn(g, dot);
+    if (p == 0) {
+        unit[3 * q] = ux;
+        unit[3 * q + 1] = uy;
+        unit[3 * q + 2] = uz;
+    }
+}
+
+// W[q][p*B + k] = exp(2 pi i k tau[q][p] / N)  (Eq. 4, Eq. 8), complex64.
+// The phase k*tau/N (in turns) is reduced to [-1/2, 1/2] in FP64 before sincospi.
+__global__ void w_kernel(const double *__restrict__ tau, int Q, int P, int B, int N,
+                         float2 *__restrict__ W) {
+    const long long L = (long long)P * B;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Q * L) return;
+    const long long q = idx / L;
+    const int l = (int)(idx % L);
+    const int p = l / B, k = l % B;
+    const double turns = (double)k * tau[q * P + p] / (double)N;
+    const double r = turns - rint(turns);
+    double s, co;
+    sincospi(2.0 * r, &s, &co);
+    W[idx] = make_float2((float)co, (float)s);
+}
+
+int launch_tau(const sp_steering *st, cudaStream_t s) {
+    sp_steering *m = const_cast<sp_steering *>(st);
+    SP_TRY(m->tau.reserve((size_t)st->Q * st->P * 8));
+    SP_TRY(m->d_mic.reserve((size_t)st->M * 3 * 8));
+    SP_TRY(m->d_dirs.reserve((size_t)st->Q * 3 * 8));
+    DevBuf d_dirs_in, d_pairs;
+    SP_TRY(d_dirs_in.reserve((size_t)st->Q * 3 * 8));
+    SP_TRY(d_pairs.reserve((size_t)st->P * 2 * 4));
+    SP_CUDA(cudaMemcpy(m->d_mic.p, st->mic.data(), st->mic.size() * 8, cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMemcpy(d_dirs_in.p, st->dirs.data(), st->dirs.size() * 8, cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMemcpy(d_pairs.p, st->pair_i.data(), st->P * 4, cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMemcpy(d_pairs.as<int>() + st->P, st->pair_j.data(), st->P * 4, cudaMemcpyHostToDevice));
+    const long long n = (long long)st->Q * st->P;
+    tau_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        m->d_mic.as<double>(), d_dirs_in.as<double>(), d_pairs.as<int>(), d_pairs.as<int>() + st->P,
+        st->Q, st->P, st->fs, st->c, m->tau.as<double>(), m->d_dirs.as<double>());
+    SP_CUDA(cudaGetLastError());
+    SP_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed on return
+    return SP_OK;
+}
+
+int launch_w(const sp_steering *st, cudaStream_t s) {
+    sp_steering *m = const_cast<sp_steering *>(st);
+    const long long n = (long long)st->Q * st->L;
+    SP_TRY(m->W.reserve((size_t)n * 8));
+    w_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(st->tau.as<double>(), st->Q, st->P, st->B,
+                                                         st->N, m->W.as<float2>());
+    SP_CUDA(cudaGetLastError());
+    m->has_w = true;
+    return SP_OK;
+}
+
+}  // namespace sp

@@ -1,0 +1,78 @@
+"""The C ABI builds and loads on the host, exports every entry point include/svdphat.h
+declares, and rejects bad arguments before touching the GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import paper_1811_11785_gb300 as sp
+from paper_1811_11785_gb300 import api
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "svdphat.h")
+
+
+def header_functions():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sp_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return sp.lib()
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ["sp_build_steering", "sp_svd_reduce", "sp_localize", "sp_phat", "sp_project",
+                 "sp_localize_srp", "sp_localize_host", "sp_last_error", "sp_check_status"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+    assert set(header_functions()) == set(api.exported_symbols())
+
+
+def test_version_and_error_string(lib):
+    assert lib.sp_version() >= 100
+    assert isinstance(lib.sp_last_error(), bytes)
+
+
+def _bs(lib, M=3, Q=4, N=16, fs=16000.0, c=343.0, flags=0, null_out=False, zero_dir=False):
+    mic = np.zeros((M, 3))
+    mic[:, 0] = np.arange(M) * 0.01
+    d = np.tile([0.0, 0.0, 1.0], (max(Q, 1), 1))
+    if zero_dir:
+        d[0] = 0.0
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    return lib.sp_build_steering(mic.ctypes.data_as(dp), M, d.ctypes.data_as(dp), Q, fs, c, N, flags,
+                                 None if null_out else ctypes.byref(h))
+
+
+@pytest.mark.parametrize("kw", [dict(M=1), dict(M=65), dict(Q=0), dict(N=15), dict(N=2), dict(fs=0.0),
+                                dict(c=-1.0), dict(flags=8), dict(null_out=True), dict(zero_dir=True)])
+def test_build_steering_rejects_bad_arguments(lib, kw):
+    assert _bs(lib, **kw) == api.SP_EINVAL
+    assert len(lib.sp_last_error()) > 0
+
+
+def test_other_entry_points_reject_null_handles(lib):
+    assert lib.sp_svd_reduce(None, 1e-5, 0, None, None) == api.SP_EINVAL
+    out = ctypes.c_void_p()
+    assert lib.sp_svd_reduce(None, 1e-5, 0, ctypes.byref(out), None) == api.SP_EINVAL
+    assert lib.sp_localize(None, None, 4, 1, 1, None, None, None, None) == api.SP_EINVAL
+    assert lib.sp_localize_srp(None, None, 4, None, None, None) == api.SP_EINVAL
+    assert lib.sp_project(None, None, 4, 1, None, None) == api.SP_EINVAL
+    assert lib.sp_phat(None, -1, 3, 5, None, None) == api.SP_EINVAL
+    assert lib.sp_phat(None, 0, 3, 5, None, None) == api.SP_OK  # T = 0 is a no-op
+    assert lib.sp_phat(None, 2, 1, 5, None, None) == api.SP_EINVAL
+    assert lib.sp_basis_info(None, None, None, None, 0) == api.SP_EINVAL
+    lib.sp_steering_destroy(None)
+    lib.sp_basis_destroy(None)

@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances (scores are normalised by L = P(N/2+1), the bound on |Y_q|):
+  * TDOA table: bit-exact.  W, PHAT: FP32 rounding (<= 2e-7 absolute, unit-modulus values).
+  * argmax indices: identical direction class wherever the oracle's top-2 margin exceeds
+    1e-4 (relative), and >= 99.5 % class agreement over all frames.
+  * FP32 scores: |dY| <= 1e-5 L.  FP16 / BF16 after FP32 rescoring: 2e-3 L / 1e-2 L.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1811_11785_gb300 as sp
+from paper_1811_11785_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+
+
+def _setup(name, T):
+    key = (name, T)
+    if key in _CACHE:
+        return _CACHE[key]
+    import __graft_entry__
+    __graft_entry__.build()
+    wl = I.workload(name, T=T)
+    tau = O.tdoa_farfield(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"])
+    W = O.steering(tau, wl["N"])
+    ob = O.svd_basis(W, wl["delta"])
+    X = O.phat(wl["frames"])
+    Z = O.project(ob["V"], X)
+    Ysvd = O.svd_scores(ob["D"], Z)
+    Ysrp = O.srp_scores(W, X)
+    cls = O.direction_classes(tau)
+    st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"], materialize_w=True)
+    b = sp.svd_reduce(st, wl["delta"])
+    frames = torch.from_numpy(wl["frames"]).cuda()
+    d = dict(wl=wl, tau=tau, W=W, ob=ob, X=X, Z=Z, Ysvd=Ysvd, Ysrp=Ysrp, cls=cls, st=st, b=b, frames=frames,
+             L=W.shape[1])
+    _CACHE[key] = d
+    return d
+
+
+CONFIGS = [("linear_q642", 100), ("planar_q2562", 777)]
+
+
+def _agree(d, idx, Y, margin_tol=1e-4, min_agree=0.995):
+    cls = d["cls"]
+    ref, _ = O.argmax_lowest(Y)
+    m = O.top2_margin(Y, cls)
+    same = cls[idx] == cls[ref]
+    big = m > margin_tol
+    assert np.all(same[big]), f"{np.sum(~same[big])} frames with margin > {margin_tol} disagree"
+    assert np.mean(same) >= min_agree, np.mean(same)
+    return np.mean(same)
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+def test_tau_table_bit_exact(name, T):
+    d = _setup(name, T)
+    assert np.array_equal(d["st"].tau(), d["tau"])
+
+
+def test_tau_bit_exact_random_geometry():
+    import __graft_entry__
+    __graft_entry__.build()
+    rng = np.random.default_rng(12)
+    mic = I.array_random_ball(rng, 9)
+    dirs = rng.standard_normal((1000, 3)) * rng.uniform(0.1, 10, size=(1000, 1))
+    st = sp.build_steering(mic, dirs, 44100.0, 340.5, 256)
+    assert np.array_equal(st.tau(), O.tdoa_farfield(mic, dirs, 44100.0, 340.5))
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+def test_steering_w(name, T):
+    d = _setup(name, T)
+    W = d["st"].w().cpu().numpy()
+    assert np.max(np.abs(W - d["W"])) < 2e-7
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+def test_phat(name, T):
+    d = _setup(name, T)
+    X = sp.phat(d["frames"]).cpu().numpy()
+    assert np.max(np.abs(X - d["X"])) < 2e-6
+
+
+def test_phat_zero_entries():
+    import __graft_entry__
+    __graft_entry__.build()
+    rng = np.random.default_rng(13)
+    F = (rng.standard_normal((3, 4, 9)) + 1j * rng.standard_normal((3, 4, 9))).astype(np.complex64)
+    F[1, 2, :] = 0
+    F[2, 0, 4] = 0
+    X = sp.phat(torch.from_numpy(F).cuda()).cpu().numpy()
+    assert np.max(np.abs(X - O.phat(F))) < 2e-6
+    assert np.all(X[1].reshape(6, 9)[[1, 3, 5]] == 0)
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+def test_svd_reduce_matches_oracle(name, T):
+    d = _setup(name, T)
+    b, ob = d["b"], d["ob"]
+    assert b.K == ob["K"]
+    s2 = b.sigma2()[: b.K]
+    assert np.max(np.abs(s2 - ob["sigma2"][: b.K]) / ob["sigma2"][0]) < 1e-9
+    V = b.V()
+    G = ob["V"].conj().T @ V                      # same subspace <=> unitary K x K
+    assert np.max(np.abs(G.conj().T @ G - np.eye(b.K))) < 1e-8
+    assert np.max(np.abs(V.conj().T @ V - np.eye(b.K))) < 1e-10
+    assert np.max(np.abs(b.D() - d["W"] @ V)) < 1e-8 * np.sqrt(d["L"])
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 1e-4), ("bf16", 1e-3)])
+def test_project(name, T, prec, tol):
+    d = _setup(name, T)
+    Zg = sp.project(d["b"], d["frames"], prec).cpu().numpy()
+    Zr = O.project(d["b"].V(), d["X"])   # the library's own basis: Z depends on V's phases
+    assert np.max(np.abs(Zg - Zr)) <= tol * np.sqrt(d["L"])
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+def test_localize_srp(name, T):
+    d = _setup(name, T)
+    idx, best = sp.localize_srp(d["st"], d["frames"])
+    idx = idx.cpu().numpy()
+    _agree(d, idx, d["Ysrp"])
+    ref = d["Ysrp"][np.arange(T), idx]
+    assert np.max(np.abs(best.cpu().numpy() - ref)) <= 1e-5 * d["L"]
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 1e-2)])
+def test_localize_svd_exhaustive(name, T, prec, tol):
+    d = _setup(name, T)
+    idx, score, proj = sp.localize(d["b"], d["frames"], "svd_exhaustive", prec)
+    torch.cuda.synchronize()
+    sp.check_status()
+    idx = idx.cpu().numpy()
+    _agree(d, idx, d["Ysvd"])
+    assert np.max(np.abs(proj.cpu().numpy() - d["Ysvd"][np.arange(T), idx])) <= tol * d["L"]
+    sref = O.score_row(d["tau"], idx, d["X"], d["wl"]["N"])       # Algorithm 1 online step 4
+    assert np.max(np.abs(score.cpu().numpy() - sref)) <= 2e-5 * d["L"]
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_localize_kdtree(name, T, prec):
+    d = _setup(name, T)
+    b = d["b"]
+    idx, _, proj = sp.localize(b, d["frames"], "svd_kdtree", prec, score=False)
+    idx = idx.cpu().numpy()
+    # exact search: the brute-force neighbour of the GPU's own query
+    Zg = sp.project(b, d["frames"], prec).cpu().numpy()
+    D = b.D()
+    Dhat = D / np.linalg.norm(D, axis=1, keepdims=True)
+    nn, d2 = O.nn_brute(Dhat, Zg)
+    Zh = np.conj(Zg / np.linalg.norm(Zg, axis=1, keepdims=True))
+    dist = np.sum(np.abs(Dhat[None, :, :] - Zh[:, None, :]) ** 2, axis=2)
+    cls = d["cls"]
+    dsec = np.where(cls[None, :] == cls[nn][:, None], np.inf, dist).min(axis=1)
+    clear = dsec - d2 > 1e-5
+    assert np.all(cls[idx[clear]] == cls[nn[clear]])
+    # against the oracle's own normalised search (Eq. 15) on its FP64 query
+    ref, _ = O.nn_brute(d["ob"]["Dhat"], d["Z"])
+    assert np.mean(cls[idx] == cls[ref]) >= 0.995
+    assert np.max(np.abs(proj.cpu().numpy() - (1 - d2 / 2))) < 1e-4
+
+
+def test_tree_shape():
+    d = _setup("planar_q2562", 777)
+    info = d["b"].kdtree_info()
+    assert info["leaf_size"] == 32 and info["n_nodes"] >= 2 * (2562 // 32) - 1
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_ragged_batches_are_consistent(prec):
+    d = _setup("planar_q2562", 777)
+    full, _, pfull = sp.localize(d["b"], d["frames"], "svd_exhaustive", prec, score=False)
+    for lo, hi in [(0, 1), (5, 132), (128, 256), (700, 777), (3, 3)]:
+        idx, _, pj = sp.localize(d["b"], d["frames"][lo:hi].contiguous(), "svd_exhaustive", prec, score=False)
+        assert torch.equal(idx, full[lo:hi])
+        assert torch.equal(pj, pfull[lo:hi])
+
+
+def test_zero_and_nan_frames():
+    d = _setup("linear_q642", 100)
+    fr = d["frames"][:6].clone()
+    fr[1] = 0                                   # silent frame: every cross spectrum is 0
+    fr[2, :, 10] = float("nan")
+    for prec in ["fp32", "fp16"]:
+        idx, score, proj = sp.localize(d["b"], fr, "svd_exhaustive", prec)
+        idx = idx.cpu().numpy()
+        assert idx[1] >= 0 and abs(float(proj[1])) < 1e-6
+        kidx, _, _ = sp.localize(d["b"], fr, "svd_kdtree", prec, score=False)
+        assert int(kidx[1]) == -1              # ||Z|| = 0: no direction
+    torch.cuda.synchronize()
+
+
+def test_host_path_matches_device():
+    d = _setup("planar_q2562", 777)
+    fh = d["frames"].cpu().pin_memory()
+    for prec in ["fp16", "fp32"]:
+        i1, s1, p1 = sp.localize(d["b"], d["frames"], "svd_exhaustive", prec)
+        i2, s2, p2 = sp.localize_host(d["b"], fh, "svd_exhaustive", prec, chunk_frames=200)
+        assert torch.equal(i1.cpu(), i2)
+        assert torch.equal(p1.cpu(), p2)
+        assert torch.allclose(s1.cpu(), s2)
+
+
+def test_bounded_wait_reports_timeout():
+    d = _setup("linear_q642", 100)
+    try:
+        sp.set_wait_budget(1)
+        sp.localize(d["b"], d["frames"], "svd_exhaustive", "fp16", score=False)
+        with pytest.raises(sp.SvdPhatError) as e:
+            sp.check_status()
+        assert e.value.code == -4
+    finally:
+        sp.set_wait_budget(0)
+    idx, _, _ = sp.localize(d["b"], d["frames"], "svd_exhaustive", "fp16", score=False)
+    sp.check_status()
+    _agree(d, idx.cpu().numpy(), d["Ysvd"])
+
+
+def test_bench_workload_full_size_sampled():
+    """The measured workload at full size (65,536 frames, planar array, Q = 2562) in the launch
+    configuration the benchmark times; 384 sampled frames are checked against the oracle."""
+    import __graft_entry__
+    __graft_entry__.build()
+    wl = I.workload("planar_q2562")
+    st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"])
+    b = sp.svd_reduce(st, wl["delta"])
+    frames = torch.from_numpy(wl["frames"]).cuda()
+    rng = np.random.default_rng(14)
+    sel = np.sort(rng.choice(frames.shape[0], 384, replace=False))
+    tau = O.tdoa_farfield(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"])
+    W = O.steering(tau, wl["N"])
+    ob = O.svd_basis(W, wl["delta"])
+    X = O.phat(wl["frames"][sel])
+    Y = O.svd_scores(ob["D"], O.project(ob["V"], X))
+    d = dict(cls=O.direction_classes(tau))
+    for prec in ["fp16", "bf16"]:
+        idx, score, proj = sp.localize(b, frames, "svd_exhaustive", prec)
+        torch.cuda.synchronize()
+        sp.check_status()
+        idx = idx.cpu().numpy()[sel]
+        _agree(d, idx, Y)
+        sref = O.score_row(tau, idx, X, wl["N"])
+        assert np.max(np.abs(score.cpu().numpy()[sel] - sref)) <= 2e-5 * W.shape[1]
