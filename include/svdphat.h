@@ -90,6 +90,15 @@ int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q,
 /* Dimensions of a steering handle; any pointer may be NULL. */
 int sp_steering_dims(const sp_steering *st, int *M, int *P, int *Q, int *N, int *B);
 
+/* Direction classes: q and q' are one class when max_p |tau[q][p] - tau[q'][p]| <= 1e-9
+ * samples; their rows of W (Eq. 8) are then identical, so every SRP-PHAT or SVD-PHAT
+ * score is the same for both (a line array cannot tell directions on a cone apart, a
+ * planar array mirror images).  The SVD-PHAT searches evaluate each class once, at its
+ * lowest index, so they return the lowest index of the winning class.
+ * n_classes (may be NULL) receives the number of classes; rep_of_host (Q int32, may be
+ * NULL) receives, for every q, the lowest index of its class. */
+int sp_steering_classes(const sp_steering *st, int *n_classes, int32_t *rep_of_host);
+
 /* Copy the FP64 TDOA table (Q x P, row-major) to host memory. Synchronous. */
 int sp_steering_tau(const sp_steering *st, double *tau_host);
 

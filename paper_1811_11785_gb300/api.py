@@ -39,6 +39,7 @@ _SIGS = {
     "sp_build_steering": ([_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
     "sp_steering_dims": ([_vp, _ip, _ip, _ip, _ip, _ip], ctypes.c_int),
+    "sp_steering_classes": ([_vp, _ip, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "sp_steering_tau": ([_vp, _dp], ctypes.c_int),
     "sp_steering_w": ([_vp, _vp, _vp], ctypes.c_int),
     "sp_steering_destroy": ([_vp], None),
@@ -134,6 +135,13 @@ class Steering:
     @property
     def handle(self):
         return self._h
+
+    def classes(self) -> np.ndarray:
+        """For every direction, the lowest index of its class (identical TDOA vectors)."""
+        out = np.empty(self.Q, dtype=np.int32)
+        _check("sp_steering_classes", lib().sp_steering_classes(
+            self._h, None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
 
     def tau(self) -> np.ndarray:
         out = np.empty((self.Q, self.P), dtype=np.float64)

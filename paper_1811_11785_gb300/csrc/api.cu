@@ -99,6 +99,7 @@ int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q, d
                                    cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = fail(SP_ECUDA, std::string("build_steering: ") + cudaGetErrorString(e));
     }
+    if (rc == SP_OK) rc = build_classes(st);
     if (rc != SP_OK) {
         delete st;
         return rc;
@@ -114,6 +115,13 @@ int sp_steering_dims(const sp_steering *st, int *M, int *P, int *Q, int *N, int 
     if (Q) *Q = st->Q;
     if (N) *N = st->N;
     if (B) *B = st->B;
+    return SP_OK;
+}
+
+int sp_steering_classes(const sp_steering *st, int *n_classes, int32_t *rep_of_host) {
+    SP_CHECK(st, SP_EINVAL, "sp_steering_classes: null handle");
+    if (n_classes) *n_classes = (int)st->reps.size();
+    if (rep_of_host) std::memcpy(rep_of_host, st->rep_of.data(), st->rep_of.size() * sizeof(int32_t));
     return SP_OK;
 }
 
@@ -224,7 +232,7 @@ int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec, v
         return launch_project_f32(b, b->work.p, T, z_dev, s);
     }
     SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "sp_project: bad precision");
-    return launch_svd_tc(b, frames_dev, T, (int)prec, nullptr, nullptr, z_dev, s);
+    return launch_svd_proj(b, frames_dev, T, (int)prec, z_dev, nullptr, s);
 }
 
 static int srp_path(const sp_steering *st, const void *frames, int T, int32_t *idx, float *best,
@@ -267,7 +275,11 @@ int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
                                            idx_dev, proj_score_dev, s));
             } else {
                 SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "bad precision");
-                SP_TRY(launch_svd_tc(b, frames_dev, T, (int)prec, idx_dev, proj_score_dev, nullptr, s));
+                const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
+                SP_TRY(b->work.reserve(zbytes + (size_t)T * 4));
+                float *zn2 = reinterpret_cast<float *>(b->work.as<char>() + zbytes);
+                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, b->work.p, zn2, s));
+                SP_TRY(launch_svd_scan(b, b->work.p, zn2, T, (int)prec, idx_dev, proj_score_dev, s));
             }
             break;
         }
@@ -283,7 +295,7 @@ int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
             } else {
                 SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "bad precision");
                 SP_TRY(b->work.reserve(zbytes));
-                SP_TRY(launch_svd_tc(b, frames_dev, T, (int)prec, nullptr, nullptr, b->work.p, s));
+                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, b->work.p, nullptr, s));
                 SP_TRY(launch_kdtree(b, b->work.p, T, idx_dev, proj_score_dev, s));
             }
             break;

@@ -100,6 +100,12 @@ struct sp_steering {
     std::vector<double> mic, dirs;      // host copies (M x 3, Q x 3)
     std::vector<int> pair_i, pair_j;    // Eq. 7 pair order
     std::vector<double> tau_host;       // Q x P
+    // Directions whose TDOA vectors agree within 1e-9 samples have identical rows of W
+    // (and of D), hence identical scores for every observation; each such class is
+    // scanned once, at its lowest index.  reps: the class representatives, ascending.
+    std::vector<int> rep_of;            // Q: representative (lowest index) of q's class
+    std::vector<int> reps;              // n_classes representatives
+    sp::DevBuf d_reps;                  // int32 [n_classes]
     sp::DevBuf tau;                     // Q x P double
     sp::DevBuf d_mic;                   // M x 3 double
     sp::DevBuf d_dirs;                  // Q x 3 double (unit directions, for step 4)
@@ -117,6 +123,7 @@ struct sp_basis {
     // device copies
     sp::DevBuf Vc32;                    // V^T as complex64 [K][L], column l = p*B + k (Eq. 7 order)
     sp::DevBuf Dc32;                    // D as complex64 [Q][K]
+    sp::DevBuf Dc32r;                   // D rows of the class representatives [n_classes][K]
     sp::TcLayout tc;
     sp::DevBuf Vtc[2];                  // GEMM1 B operand, fp16 [0] / bf16 [1]: [n1][row_elems]
     sp::DevBuf Dtc[2];                  // GEMM2 B operand, fp16 / bf16: [Q][k2_atoms*64]
@@ -157,11 +164,16 @@ int launch_svd_scan_f32(const sp_basis *b, const void *Z, int T, uint64_t *keys,
                         float *best, cudaStream_t s);
 int launch_score_row(const sp_steering *st, const void *frames, int T, const int32_t *idx,
                      float *score, cudaStream_t s);
-int launch_svd_tc(const sp_basis *b, const void *frames, int T, int prec, int32_t *idx,
-                  float *proj, void *z_out, cudaStream_t s);
+// tensor-core path: Z = V^H X (PHAT fused) into z_out [T][K] complex64, then the Re{D Z} scan
+// (zn2_out [T] receives ||Z||^2 per frame, may be null; the scan needs it)
+int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
+                    cudaStream_t s);
+int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
+                    float *proj, cudaStream_t s);
 int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
                   cudaStream_t s);
 int tc_prepare(sp_basis *b);   // upload GEMM1/GEMM2 operands in the tensor-core layouts
 int reduce_basis(const sp_steering *st, double delta, sp_basis *b);
 int build_kdtree(sp_basis *b);
+int build_classes(sp_steering *st);   // rep_of / reps from the TDOA table (host)
 }  // namespace sp

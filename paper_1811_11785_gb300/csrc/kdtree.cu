@@ -6,8 +6,10 @@
 // searched in the real 2K-dimensional embedding x_q = [Re D^_q, Im D^_q] with query
 // [Re Z^, -Im Z^].
 //
-// Build (host): split on the dimension of largest spread at the median (ties broken by
-// index), recursively, until a node holds at most 32 points (one leaf bucket = one warp).
+// Build (host): one point per direction class (directions with identical TDOA vectors
+// have identical rows D_q); split on the dimension of largest spread at the median (ties
+// broken by index), recursively, until a node holds at most 32 points (one leaf bucket =
+// one warp).
 // Search (device): one warp per query; the warp walks the tree with an explicit stack,
 // visiting the near child first and keeping the far child only if the squared distance
 // from the query to the splitting plane does not exceed the best distance so far
@@ -95,9 +97,8 @@ int build_kdtree(sp_basis *b) {
     Builder bd;
     bd.dim = dim;
     bd.pts = &pts;
-    std::vector<int> ids(Q);
-    std::iota(ids.begin(), ids.end(), 0);
-    bd.build(ids, 0, Q, 0);
+    std::vector<int> ids(b->st->reps);   // one point per direction class (identical rows)
+    bd.build(ids, 0, (int)ids.size(), 0);
     SP_CHECK(bd.depth <= kMaxDepth, SP_ENOTIMPL, "k-d tree too deep");
     const int nb = (int)(bd.bucket_ids.size() / kLeaf);
     std::vector<float> leaf((size_t)nb * dim * kLeaf, 1e18f);

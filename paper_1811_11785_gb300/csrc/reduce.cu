@@ -304,6 +304,12 @@ int reduce_basis(const sp_steering *st, double delta, sp_basis *b) {
             dc[2 * i] = (float)D[i].real();
             dc[2 * i + 1] = (float)D[i].imag();
         }
+        const int nr = (int)st->reps.size();
+        std::vector<float> dcr((size_t)nr * K * 2);
+        for (int r = 0; r < nr; ++r)
+            for (int k = 0; k < 2 * K; ++k) dcr[(size_t)r * K * 2 + k] = dc[(size_t)st->reps[r] * K * 2 + k];
+        SP_TRY(b->Dc32r.reserve(dcr.size() * 4));
+        SP_CUDA(cudaMemcpy(b->Dc32r.p, dcr.data(), dcr.size() * 4, cudaMemcpyHostToDevice));
         SP_TRY(b->Vc32.reserve(vt.size() * 4));
         SP_TRY(b->Dc32.reserve(dc.size() * 4));
         SP_CUDA(cudaMemcpy(b->Vc32.p, vt.data(), vt.size() * 4, cudaMemcpyHostToDevice));

@@ -74,11 +74,13 @@ __device__ __forceinline__ float key_score(unsigned long long k) {
 }
 
 __global__ void finalize_keys_kernel(const unsigned long long *__restrict__ keys, int T,
-                                     int32_t *__restrict__ idx, float *__restrict__ best) {
+                                     const int32_t *__restrict__ remap, int32_t *__restrict__ idx,
+                                     float *__restrict__ best) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const unsigned long long k = keys[t];
-    idx[t] = k ? (int32_t)(~(uint32_t)k) : -1;
+    const int32_t r = (int32_t)(~(uint32_t)k);
+    idx[t] = k ? (remap ? remap[r] : r) : -1;
     if (best) best[t] = k ? key_score(k) : __int_as_float(0x7fc00000);
 }
 
@@ -192,8 +194,8 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
-int launch_srp_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint64_t *keys,
-                      int32_t *idx, float *best, cudaStream_t s) {
+static int launch_re_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint64_t *keys,
+                            const int32_t *remap, int32_t *idx, float *best, cudaStream_t s) {
     if (T == 0) return SP_OK;
     SP_CUDA(cudaMemsetAsync(keys, 0, (size_t)T * 8, s));
     const int nq = (Qa + RA_M - 1) / RA_M;
@@ -202,14 +204,21 @@ int launch_srp_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint6
                                                           (const float2 *)X, T, nq,
                                                           (unsigned long long *)keys);
     SP_CUDA(cudaGetLastError());
-    finalize_keys_kernel<<<(T + 255) / 256, 256, 0, s>>>((const unsigned long long *)keys, T, idx, best);
+    finalize_keys_kernel<<<(T + 255) / 256, 256, 0, s>>>((const unsigned long long *)keys, T, remap, idx, best);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
+int launch_srp_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint64_t *keys,
+                      int32_t *idx, float *best, cudaStream_t s) {
+    return launch_re_argmax(A, Qa, Lc, X, T, keys, nullptr, idx, best, s);
+}
+
+// FP32 exhaustive scan Re{D Z} (Eq. 14) over the class representatives only.
 int launch_svd_scan_f32(const sp_basis *b, const void *Z, int T, uint64_t *keys, int32_t *idx,
                         float *best, cudaStream_t s) {
-    return launch_srp_argmax(b->Dc32.p, b->st->Q, b->K, Z, T, keys, idx, best, s);
+    return launch_re_argmax(b->Dc32r.p, (int)b->st->reps.size(), b->K, Z, T, keys, b->st->d_reps.as<int32_t>(),
+                            idx, best, s);
 }
 
 // ------------------------------------------------------------------------- Z = V^H X (FP32)
@@ -296,9 +305,13 @@ int launch_project_f32(const sp_basis *b, const void *X, int T, void *Z, cudaStr
 // d_m = fs/c r_m . u_q, every term factors as W_ij X_ij = y_i conj(y_j) with
 // y_m[k] = x^_m[k] exp(-2 pi i k d_m / N), so
 //     sum_{i<j} Re{y_i conj(y_j)} = (|sum_m y_m|^2 - sum_m |y_m|^2) / 2
-// per bin: O(M) work per bin instead of O(P).  One warp per frame, lanes along k.
+// per bin: O(M) work per bin instead of O(P).  One warp per frame, lane l takes bins
+// l, l + 32, ...; the phasor of mic m at bin k is advanced by exp(-2 pi i 32 d_m / N) from
+// one bin of the lane to the next (one sincospi pair per mic and lane, fresh per frame).
+// d_m is formed in FP64 once per mic by lane m and broadcast.
+template <int MMAX>
 __global__ void __launch_bounds__(256)
-    score_row_kernel(const float2 *__restrict__ frames, int T, int M, int B, int N,
+    score_row_kernel(const float2 *__restrict__ frames, int T, int M, int B, double inv_n,
                      const double *__restrict__ unit, const double *__restrict__ mic, double g,
                      const int32_t *__restrict__ idx, float *__restrict__ score) {
     const int lane = threadIdx.x & 31;
@@ -309,43 +322,67 @@ __global__ void __launch_bounds__(256)
         if (lane == 0) score[t] = __int_as_float(0x7fc00000);
         return;
     }
-    // per-mic advance in turns per bin, split hi + lo so that k * e is exact to ~1e-9 turns
-    float ehi[16], elo[16];
+    // lane m < M: advance of mic m in turns per bin, e = d_m / N (FP64), split hi + lo
+    float my_hi = 0.f, my_lo = 0.f;
+    if (lane < M) {
+        const double d = g * ((mic[3 * lane] * unit[3 * q] + mic[3 * lane + 1] * unit[3 * q + 1]) +
+                              mic[3 * lane + 2] * unit[3 * q + 2]);
+        const double e = d * inv_n;
+        my_hi = (float)e;
+        my_lo = (float)(e - (double)my_hi);
+    }
+    const float2 *fr = frames + (size_t)t * M * B;
+    float acc = 0.f;
+    float2 ph[MMAX], stp[MMAX];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < MMAX; ++m) {
+        const float ehi = __shfl_sync(0xffffffffu, my_hi, m);
+        const float elo = __shfl_sync(0xffffffffu, my_lo, m);
         if (m < M) {
-            const double d = g * ((mic[3 * m] * unit[3 * q] + mic[3 * m + 1] * unit[3 * q + 1]) +
-                                  mic[3 * m + 2] * unit[3 * q + 2]);
-            const double e = d / (double)N;
-            ehi[m] = (float)e;
-            elo[m] = (float)(e - (double)ehi[m]);
+            // phase of bin `lane` and of a 32-bin step, reduced to [-1/2, 1/2] turns
+            const float kf = (float)lane;
+            float p0 = kf * ehi;
+            const float r0 = (p0 - rintf(p0)) + fmaf(kf, elo, fmaf(kf, ehi, -p0));
+            float p1 = 32.f * ehi;
+            const float r1 = (p1 - rintf(p1)) + 32.f * elo;
+            float s, c;
+            sincospif(-2.f * r0, &s, &c);
+            ph[m] = make_float2(c, s);
+            sincospif(-2.f * r1, &s, &c);
+            stp[m] = make_float2(c, s);
         }
     }
-    float acc = 0.f;
-    for (int k = lane; k < B; k += 32) {
-        const float kf = (float)k;
-        float sr = 0.f, si = 0.f, en = 0.f;
+    // three bins per lane per round: 3 * M independent loads in flight
+    for (int k0 = lane; k0 < B; k0 += 96) {
+        float2 v[3][MMAX];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            if (m < M) {
-                const float2 v = __ldg(frames + ((size_t)t * M + m) * B + k);
-                const float mag2 = v.x * v.x + v.y * v.y;
-                if (mag2 >= kZeroMag2) {
-                    const float r = rsqrtf(mag2);
-                    const float xr = v.x * r, xi = v.y * r;
-                    const float ph = kf * ehi[m];
-                    const float err = fmaf(kf, ehi[m], -ph);
-                    const float turns = (ph - rintf(ph)) + fmaf(kf, elo[m], err);
-                    float sn, cs;
-                    sincospif(-2.f * turns, &sn, &cs);
-                    const float yr = xr * cs - xi * sn, yi = xr * sn + xi * cs;
-                    sr += yr;
-                    si += yi;
-                    en += yr * yr + yi * yi;
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int m = 0; m < MMAX; ++m)
+                v[u][m] = (m < M && k0 + 32 * u < B) ? __ldg(fr + (size_t)m * B + k0 + 32 * u) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            float sr = 0.f, si = 0.f, en = 0.f;
+#pragma unroll
+            for (int m = 0; m < MMAX; ++m) {
+                if (m < M) {
+                    const float2 x = v[u][m];
+                    const float mag2 = x.x * x.x + x.y * x.y;
+                    const float2 w = ph[m];
+                    if (mag2 >= kZeroMag2) {
+                        const float r = rsqrtf(mag2);
+                        const float xr = x.x * r, xi = x.y * r;
+                        const float yr = xr * w.x - xi * w.y, yi = xr * w.y + xi * w.x;
+                        sr += yr;
+                        si += yi;
+                        en += yr * yr + yi * yi;
+                    }
+                    const float2 st = stp[m];
+                    ph[m] = make_float2(w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x);
                 }
             }
+            if (k0 + 32 * u < B) acc += 0.5f * (sr * sr + si * si - en);
         }
-        acc += 0.5f * (sr * sr + si * si - en);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -355,10 +392,11 @@ __global__ void __launch_bounds__(256)
 int launch_score_row(const sp_steering *st, const void *frames, int T, const int32_t *idx,
                      float *score, cudaStream_t s) {
     if (T == 0) return SP_OK;
+    SP_CHECK(st->M <= 16, SP_ENOTIMPL, "online step 4 supports M <= 16");
     const long long blocks = ((long long)T + 7) / 8;
-    score_row_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, st->N,
-                                                      st->d_dirs.as<double>(), st->d_mic.as<double>(),
-                                                      st->fs / st->c, idx, score);
+    auto kern = st->M <= 8 ? score_row_kernel<8> : score_row_kernel<16>;
+    kern<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, 1.0 / (double)st->N,
+                                          st->d_dirs.as<double>(), st->d_mic.as<double>(), st->fs / st->c, idx, score);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

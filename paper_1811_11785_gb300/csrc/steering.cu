@@ -2,6 +2,10 @@
 // matrix W (Eq. 4, stacked as Eq. 8).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
 #include "common.h"
 
 namespace sp {
@@ -70,6 +74,50 @@ int launch_tau(const sp_steering *st, cudaStream_t s) {
         st->Q, st->P, st->fs, st->c, m->tau.as<double>(), m->d_dirs.as<double>());
     SP_CUDA(cudaGetLastError());
     SP_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed on return
+    return SP_OK;
+}
+
+// Equivalence classes of directions: q ~ q' when max_p |tau[q][p] - tau[q'][p]| <= 1e-9
+// samples (a line array cannot tell directions on a cone apart, a planar array mirror
+// images).  Sort by the first pair's TDOA, compare rows inside the 1e-9 window, join
+// classes with union-find; each class is represented by its lowest index.
+int build_classes(sp_steering *st) {
+    const int Q = st->Q, P = st->P;
+    const double tol = 1e-9;
+    const double *tau = st->tau_host.data();
+    std::vector<int> order(Q), parent(Q);
+    std::iota(order.begin(), order.end(), 0);
+    std::iota(parent.begin(), parent.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tau[(size_t)a * P] < tau[(size_t)b * P]; });
+    auto find = [&](int x) {
+        while (parent[x] != x) {
+            parent[x] = parent[parent[x]];
+            x = parent[x];
+        }
+        return x;
+    };
+    for (int a = 0; a < Q; ++a) {
+        const int qa = order[a];
+        for (int b = a + 1; b < Q; ++b) {
+            const int qb = order[b];
+            if (tau[(size_t)qb * P] - tau[(size_t)qa * P] > tol) break;
+            bool same = true;
+            for (int p = 0; p < P && same; ++p)
+                same = std::fabs(tau[(size_t)qa * P + p] - tau[(size_t)qb * P + p]) <= tol;
+            if (same) {
+                const int ra = find(qa), rb = find(qb);
+                if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+            }
+        }
+    }
+    st->rep_of.resize(Q);
+    st->reps.clear();
+    for (int q = 0; q < Q; ++q) {
+        st->rep_of[q] = find(q);
+        if (st->rep_of[q] == q) st->reps.push_back(q);
+    }
+    SP_TRY(st->d_reps.reserve(st->reps.size() * 4));
+    SP_CUDA(cudaMemcpy(st->d_reps.p, st->reps.data(), st->reps.size() * 4, cudaMemcpyHostToDevice));
     return SP_OK;
 }
 

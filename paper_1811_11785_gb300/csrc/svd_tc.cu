@@ -1,17 +1,25 @@
-// Tensor-core SVD-PHAT (online steps 1-3 of Algorithm 1) in one kernel, sm_103a.
+// Tensor-core SVD-PHAT on sm_103a: online steps 1-3 of Algorithm 1 in two kernels.
 //
-//   GEMM1 (Eq. 12):  Z^T = X^T conj(V) as a real GEMM over 2L, M = 128 frames per CTA,
-//                    N = 2K (Re Z_k, Im Z_k interleaved), FP16 or BF16 inputs, FP32
-//                    accumulator in TMEM.  The A operand (the PHAT cross spectra, Eq. 3)
-//                    is produced straight into shared memory by 8 producer warps from the
-//                    STFT frames; X never reaches global memory.  The B operand (V, scaled
-//                    by sqrt(L)) streams from L2 by TMA.
-//   GEMM2 (Eq. 14):  Y = Re{D Z} = [Re D, -Im D] . [Re Z, Im Z] over Q tiles of 128,
-//                    FP16/BF16 inputs (Z rounded from the FP32 accumulator), FP32 in
-//                    TMEM.  Y never leaves the chip: each frame's thread keeps the 8 best
-//                    (score, q) pairs.
-//   Rescoring:       the 8 candidates are rescored in FP32 from FP32 Z and FP32 D; the best
-//                    one (ties -> lowest q) is the frame's direction.
+// svd_proj_kernel (persistent, one CTA per SM) -- Eq. 3, Eq. 7, Eq. 12:
+//   Z^T = X^T conj(V) as a real GEMM over 2L with M = 128 frames per tile, N = 2K
+//   (Re Z_k, Im Z_k interleaved), FP16 or BF16 operands, FP32 accumulator in TMEM.  The A
+//   operand (the PHAT cross spectra) is produced straight into shared memory by 16 producer
+//   warps (one thread per frame and bin) from the STFT frames, so X never reaches global
+//   memory; V (scaled by sqrt(L))
+//   streams from L2 by TMA.  Four epilogue warps drain each finished tile's Z from TMEM
+//   (double-buffered) to global memory as FP32 while the producers stream the next tile.
+//
+// svd_scan_kernel -- Eq. 13, Eq. 14 and the rescoring:
+//   Y = Re{D Z} = [Re D, -Im D] . [Re Z, Im Z] over tiles of 64 direction classes, FP16/BF16
+//   operands (Z rounded from FP32), FP32 in TMEM; Y never leaves the chip.  Pass 1 keeps each
+//   frame's maximum m.  Every scan score differs from its FP32 rescoring by at most
+//   e = 2.1 u sqrt(L) ||Z|| (u: unit roundoff of the operand type; sum_k |D_qk||Z_k| <=
+//   ||D_q|| ||Z|| and ||D_q|| <= ||W_q|| = sqrt(L)), so the FP32 winner scores at least
+//   m - 2e in the scan.  Pass 2 recomputes the scan and collects every class at or above
+//   m - 2e - 1e-6 L (at most 16 per frame; a frame with more is rescored against every
+//   class).  All collected classes are rescored in FP32 against FP32 Z and FP32 D; the best
+//   (ties -> lowest direction index) is the frame's direction.  The result equals an FP32
+//   scan of the same Z.
 //
 // K-dimension layout of GEMM1 (a permutation of the paper's column order p*B + k): the
 // contraction is cut into stages (bin chunk c of 4 bins, pair group g of <= 24 pairs);
@@ -19,10 +27,9 @@
 // p*8 + 2b + 1 (imaginary), so one K16 MMA step covers 2 pairs x 4 bins and a 64-element
 // 128-byte-swizzled atom covers 8 pairs.
 //
-// Warp roles (384 threads): warps 0-7 produce A tiles (and warps 0-3 are the epilogue),
-// warp 8 issues TMA loads, warp 9 allocates TMEM and issues the MMAs.  Every mbarrier
-// wait is bounded; a wait that gives up records an error in g_status and the CTA drains
-// its in-flight copies/MMAs (with a fixed generous bound) and returns.
+// Every mbarrier wait is bounded; a wait that gives up records an error in g_status and
+// the CTA drains its in-flight TMA loads and MMAs (with a fixed generous bound) before it
+// frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -58,17 +65,20 @@ constexpr int kAtomElems = 64;        // 16-bit elements per swizzle atom row
 constexpr int kAtomBytes = 128 * 128; // one 128-row atom
 constexpr int kGroupElems = 3 * kAtomElems;
 constexpr int kMaxN1 = 144;           // GEMM1 N limit of this shared-memory plan
-constexpr int kThreads = 384;
-constexpr int kProducerThreads = 256;
-constexpr int kTmemCols = 512;
-constexpr int kTmemY = 256;           // GEMM2 accumulators at columns 256 and 384
-constexpr int kTop = 8;
+constexpr int kProdWarps = 16;
+constexpr int kProjThreads = 22 * 32; // 16 producer, 4 epilogue, 1 TMA, 1 MMA warps
+constexpr int kEpiWarp0 = 16, kTmaWarp = 20, kMmaWarp = 21;
+constexpr int kZBuf = 256;            // TMEM column offset of the second Z buffer
+constexpr int kScanThreads = 256;     // 4 epilogue, 1 TMA, 1 MMA, 2 helper warps
+constexpr int kN2 = 64;               // direction classes per GEMM2 tile
+constexpr int kCap = 16;              // candidates kept per frame
+constexpr int kRing = 4;              // GEMM2 D-tile / TMEM buffers in flight
 
 TcLayout make_tc_layout(int P, int B, int K) {
     TcLayout t;
     t.P = P;
     t.Pp = (P + 1) / 2 * 2;
-    t.steps_per_chunk = 0;   // per group, computed in the kernel
+    t.steps_per_chunk = 0;
     t.atoms_per_chunk = 3;
     t.n_chunks = (B + kChunkBins - 1) / kChunkBins;
     const int G = (P + kGroupPairs - 1) / kGroupPairs;
@@ -76,66 +86,30 @@ TcLayout make_tc_layout(int P, int B, int K) {
     t.n1 = (2 * K + 15) / 16 * 16;
     t.k2 = (2 * K + 15) / 16 * 16;
     t.k2_atoms = (t.k2 + kAtomElems - 1) / kAtomElems;
-    t.n2 = 128;
+    t.n2 = kN2;
     return t;
 }
 
-struct TcParams {
-    const float2 *frames;
-    int T, M, B, P, G, n_chunks;
-    int n1, K, Q, k2, k2_atoms, nq;
-    float inv_vscale;
-    int do_scan;
-    const float2 *Dc32;  // [Q][K] complex64
-    int32_t *idx;
-    float *proj;
-    float2 *z_out;       // [T][K] complex64 or null
-};
-
-struct SmemPlan {
-    int a_stage, b_stage;          // bytes per GEMM1 stage buffer
-    int off_b;                     // offset of the B stages
-    int off_a2, off_b2, off_zf;    // GEMM2 regions (overlap GEMM1)
-    int zstride;                   // floats per Zf row
-    int off_bar;                   // barriers
-    int total;
-};
-
-static SmemPlan make_plan(const TcLayout &t) {
-    SmemPlan p;
-    p.a_stage = 3 * kAtomBytes;
-    p.b_stage = 3 * t.n1 * 128;
-    p.off_b = 2 * p.a_stage;
-    const int r0 = p.off_b + 2 * p.b_stage;
-    p.off_a2 = 0;
-    p.off_b2 = t.k2_atoms * kAtomBytes;
-    p.off_zf = p.off_b2 + 2 * t.k2_atoms * kAtomBytes;
-    p.zstride = t.n1 + 1;
-    const int r1 = p.off_zf + 128 * p.zstride * 4;
-    p.off_bar = (std::max(r0, r1) + 127) / 128 * 128;
-    p.total = p.off_bar + 256 + 1024;  // + slack for 1024-byte alignment
-    // at least 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM
-    p.total = std::max(p.total, 120 * 1024);
-    return p;
-}
-
-__device__ __forceinline__ float2 ld_stream(const float2 *p) {
-    float2 v;
-    asm volatile("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-    return v;
-}
-
-
-// The 120 pairs (i, j), i < j < 16, in Eq. 7 order; unrolled loops over this table keep
+// The pairs (i, j), i < j < MMAX, in Eq. 7 order; unrolled loops over this table keep
 // every x^_m access a compile-time register index.
-struct PairTab { int i[120]; int j[120]; };
-constexpr PairTab make_pair_tab() {
-    PairTab t{};
+template <int MMAX>
+struct PairTab {
+    int i[MMAX * (MMAX - 1) / 2];
+    int j[MMAX * (MMAX - 1) / 2];
+};
+template <int MMAX>
+constexpr PairTab<MMAX> make_pair_tab() {
+    PairTab<MMAX> t{};
     int n = 0;
-    for (int i = 0; i < 16; ++i)
-        for (int j = i + 1; j < 16; ++j) { t.i[n] = i; t.j[n] = j; ++n; }
+    for (int i = 0; i < MMAX; ++i)
+        for (int j = i + 1; j < MMAX; ++j) {
+            t.i[n] = i;
+            t.j[n] = j;
+            ++n;
+        }
     return t;
 }
+
 template <int BF16>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
     if (BF16) {
@@ -147,373 +121,497 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
-template <int BF16>
-__global__ void __launch_bounds__(kThreads, 1)
-    svd_tc_kernel(const __grid_constant__ CUtensorMap tmap_v, const __grid_constant__ CUtensorMap tmap_d,
-                  const TcParams prm) {
+__device__ __forceinline__ float2 ld_stream(const float2 *p) {
+    float2 v;
+    asm volatile("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
+// ===================================================================== GEMM1 kernel
+struct ProjParams {
+    const float2 *frames;
+    int T, M, B, P, G, n_chunks;
+    int n1, K, n_tiles;
+    float inv_vscale;
+    float2 *z_out;       // [T][K] complex64
+    float *zn2_out;      // [T] ||Z||^2 or null
+};
+
+// MMAX: bound on the microphone count (EXACT: M == MMAX, known at compile time);
+// DEPTH: how many items of raw STFT values are held in registers ahead of use.
+template <int BF16, int MMAX, bool EXACT, int DEPTH>
+__global__ void __launch_bounds__(kProjThreads, 1)
+    svd_proj_kernel(const __grid_constant__ CUtensorMap tmap_v, const ProjParams prm) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    // shared-memory plan (mirrors make_plan on the host)
     const int n1 = prm.n1;
     const int a_stage = 3 * kAtomBytes, b_stage = 3 * n1 * 128;
     const int off_b = 2 * a_stage;
-    const int off_b2 = prm.k2_atoms * kAtomBytes;
-    const int off_zf = off_b2 + 2 * prm.k2_atoms * kAtomBytes;
-    const int zstride = n1 + 1;
-    const int r0 = off_b + 2 * b_stage, r1 = off_zf + 128 * zstride * 4;
-    const int off_bar = (max(r0, r1) + 127) / 128 * 128;
+    const int off_bar = off_b + 2 * b_stage;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + off_bar);
-    uint64_t *full_a = bars + 0, *full_b = bars + 2, *empty = bars + 4, *g1_done = bars + 6;
-    uint64_t *b2_full = bars + 7, *b2_empty = bars + 9, *t2_full = bars + 11, *t2_empty = bars + 13;
-    uint64_t *drain = bars + 15;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 17);
-
+    uint64_t *full_a = bars + 0, *full_b = bars + 2, *empty = bars + 4;
+    uint64_t *zfull = bars + 6, *zempty = bars + 8, *drain = bars + 10;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 11);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 12);
     const long long budget = g_wait_budget;
-    const long long t0 = (long long)blockIdx.x * 128;
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(&full_a[i], kProducerThreads);
+            ptx::mbar_init(&full_a[i], kProdWarps);
             ptx::mbar_init(&full_b[i], 1);
             ptx::mbar_init(&empty[i], 1);
-            ptx::mbar_init(&b2_full[i], 1);
-            ptx::mbar_init(&b2_empty[i], 1);
-            ptx::mbar_init(&t2_full[i], 1);
-            ptx::mbar_init(&t2_empty[i], 128);
+            ptx::mbar_init(&zfull[i], 1);
+            ptx::mbar_init(&zempty[i], 128);
         }
-        ptx::mbar_init(g1_done, 1);
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
-    if (warp == 8 && lane == 0) {
-        ptx::prefetch_tmap(&tmap_v);
-        ptx::prefetch_tmap(&tmap_d);
-    }
-    if (warp == 9) {
-        ptx::tmem_alloc(tmem_slot, kTmemCols);
+    if (warp == kTmaWarp && lane == 0) ptx::prefetch_tmap(&tmap_v);
+    if (warp == kMmaWarp) {
+        ptx::tmem_alloc(tmem_slot, 512);
         ptx::tmem_relinquish();
     }
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int n_stages = prm.n_chunks * prm.G;
-    bool drained = false;  // MMA issuer: all issued MMAs known complete
-
+    const int stages_per_tile = prm.n_chunks * prm.G;
+    const int my_tiles = prm.n_tiles > (int)blockIdx.x ? (prm.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto give_up = [&]() {
         *abort_flag = 1;
         atomicOr(&g_status, 1);
     };
 
-    // =============================================================== GEMM1
-    if (warp < 8) {
-        // ---------------- producers: PHAT of (frame f, bins 2bp, 2bp+1) of each chunk
-        const int f = tid >> 1, bp = tid & 1;
-        const long long frame = t0 + f;
-        const bool live = frame < prm.T;
-        const float2 *fr = prm.frames + (size_t)(live ? frame : 0) * prm.M * prm.B;
-        for (int c = 0; c < prm.n_chunks; ++c) {
-            float2 xh[16][2];
+    if (warp < kProdWarps) {
+        // -------- producers: PHAT of (frame f, bin b) of every chunk of every tile.
+        // The STFT stream of this CTA is a flat sequence of items (local tile, chunk); the
+        // raw values of item j + DEPTH are in flight while item j is normalised and written.
+        // With EXACT, the pair layout (P, groups, slots) is known at compile time.
+        constexpr int NPAIR = MMAX * (MMAX - 1) / 2;
+        constexpr PairTab<MMAX> tab = make_pair_tab<MMAX>();
+        const int M = EXACT ? MMAX : prm.M;
+        const int P = EXACT ? NPAIR : prm.P;
+        const int G = EXACT ? (NPAIR + kGroupPairs - 1) / kGroupPairs : prm.G;
+        const int f = tid >> 2, b = tid & 3;
+        const int n_chunks = prm.n_chunks;
+        const size_t frame_elems = (size_t)M * prm.B;
+        // swizzled byte offset of this thread's 4 bytes in 16-byte chunk x of an atom row
+        uint32_t sw[8];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
+        for (int x = 0; x < 8; ++x) sw[x] = f * 128 + b * 4 + ((x ^ (f & 7)) << 4);
+        // load cursor: item (li, c), frame pointer, liveness
+        int ld_li = 0, ld_c = 0;
+        const float2 *ld_fr = prm.frames;
+        bool ld_live = false;
+        auto ld_seek_tile = [&]() {
+            const long long frame = (long long)((int)blockIdx.x + ld_li * (int)gridDim.x) * 128 + f;
+            ld_live = ld_li < my_tiles && frame < prm.T;
+            ld_fr = prm.frames + (ld_live ? (size_t)frame * frame_elems : 0);
+        };
+        float2 raw[DEPTH][MMAX];
+        auto load_next = [&](float2 (&dst)[MMAX]) {
+            const int k = ld_c * kChunkBins + b;
+            const bool ok = ld_live && k < prm.B;
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    xh[m][b] = make_float2(0.f, 0.f);
-                    const int k = c * kChunkBins + 2 * bp + b;
-                    if (m < prm.M && live && k < prm.B) {
-                        const float2 v = ld_stream(fr + (size_t)m * prm.B + k);
-                        const float mag2 = v.x * v.x + v.y * v.y;
-                        const float r = mag2 < 1e-30f ? 0.f : rsqrtf(mag2);
-                        xh[m][b] = make_float2(v.x * r, v.y * r);
-                    }
-                }
+            for (int m = 0; m < MMAX; ++m)
+                dst[m] = (ok && m < M) ? ld_stream(ld_fr + (size_t)m * prm.B + k) : make_float2(0.f, 0.f);
+            if (++ld_c == n_chunks) {
+                ld_c = 0;
+                ++ld_li;
+                ld_seek_tile();
             }
-            for (int g = 0; g < prm.G; ++g) {
-                const int st = c * prm.G + g;
+        };
+        ld_seek_tile();
+        const int n_items = my_tiles * n_chunks;
+        int st = 0;  // stage counter
+        // one item: normalise the raw values, start loading a later item into the same
+        // registers, then write every pair of every stage group of the item
+        auto step = [&](float2 (&cur)[MMAX]) -> bool {
+            float2 xh[MMAX];
+#pragma unroll
+            for (int m = 0; m < MMAX; ++m) {
+                const float2 v = cur[m];
+                const float mag2 = v.x * v.x + v.y * v.y;
+                const float r = mag2 < 1e-30f ? 0.f : rsqrtf(mag2);
+                xh[m] = make_float2(v.x * r, v.y * r);
+            }
+            load_next(cur);
+            for (int g = 0; g < G; ++g, ++st) {
                 const int s = st & 1;
                 const uint32_t par = ((st >> 1) & 1) ^ 1;
-                if (*abort_flag) break;
+                if (*abort_flag) return false;
                 if (!ptx::mbar_wait(&empty[s], par, budget)) {
                     give_up();
-                    break;
+                    return false;
                 }
-                uint8_t *A = smem + s * a_stage;
-                const int p_lo = g * kGroupPairs;
-                const int npg = min(kGroupPairs, prm.P - p_lo);
-                const int nslots = (npg + 1) & ~1;  // even number of pair slots written
+                const uint32_t A = ptx::smem_u32(smem + s * a_stage);
+                uint32_t ad[8];
 #pragma unroll
-                for (int pp = 0; pp < 120; ++pp) {
-                    constexpr PairTab tab = make_pair_tab(); const int i = tab.i[pp], j = tab.j[pp];
-                    if (j < prm.M) {
-                        const int p = i * prm.M - ((i * (i + 1)) >> 1) + (j - i - 1);
+                for (int x = 0; x < 8; ++x) ad[x] = A + sw[x];
+                const int p_lo = g * kGroupPairs;
+                const int npg = min(kGroupPairs, P - p_lo);
+#pragma unroll
+                for (int pp = 0; pp < NPAIR; ++pp) {
+                    const int i = tab.i[pp], jj = tab.j[pp];
+                    if (jj < M) {
+                        const int p = i * M - ((i * (i + 1)) >> 1) + (jj - i - 1);
                         const int pl = p - p_lo;
                         if (pl >= 0 && pl < npg) {
-                            const float2 a0 = xh[i][0], b0 = xh[j][0];
-                            const float2 a1 = xh[i][1], b1 = xh[j][1];
-                            const uint32_t w0 = pack2<BF16>(a0.x * b0.x + a0.y * b0.y, a0.y * b0.x - a0.x * b0.y);
-                            const uint32_t w1 = pack2<BF16>(a1.x * b1.x + a1.y * b1.y, a1.y * b1.x - a1.x * b1.y);
-                            const uint32_t off = (pl >> 3) * kAtomBytes + f * 128 +
-                                                 (((pl & 7) ^ (f & 7)) << 4) + bp * 8;
-                            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ptx::smem_u32(A + off)),
-                                         "r"(w0), "r"(w1)
+                            const float2 a0 = xh[i], b0 = xh[jj];
+                            const uint32_t w = pack2<BF16>(a0.x * b0.x + a0.y * b0.y, a0.y * b0.x - a0.x * b0.y);
+                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(ad[pl & 7] + (pl >> 3) * kAtomBytes), "r"(w)
                                          : "memory");
                         }
                     }
                 }
-                if (nslots > npg) {  // zero partner of an odd last pair
-                    const int pl = npg;
-                    const uint32_t off = (pl >> 3) * kAtomBytes + f * 128 + (((pl & 7) ^ (f & 7)) << 4) + bp * 8;
-                    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ptx::smem_u32(A + off)), "r"(0u), "r"(0u)
+                if (npg & 1)  // zero partner slot of an odd last pair
+                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(ad[npg & 7] + (npg >> 3) * kAtomBytes), "r"(0u)
                                  : "memory");
-                }
                 ptx::fence_proxy_async_smem();
-                ptx::mbar_arrive(&full_a[s]);
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&full_a[s]);
             }
-            if (*abort_flag) break;
+            return true;
+        };
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) load_next(raw[d]);
+        for (int j = 0; j < n_items; j += DEPTH) {
+            if (!step(raw[0])) break;
+            if (DEPTH > 1 && j + 1 < n_items && !step(raw[DEPTH - 1])) break;
         }
-    } else if (warp == 8) {
-        // ---------------- TMA producer for V tiles
+    } else if (warp < kEpiWarp0 + 4) {
+        // -------- epilogue: Z of each finished tile, TMEM -> FP32 global
+        const int q4 = warp - kEpiWarp0;   // TMEM lane quarter of this warp
+        const int r = q4 * 32 + lane;      // frame row within the tile
+        for (int li = 0; li < my_tiles; ++li) {
+            const int zb = li & 1;
+            if (*abort_flag) break;
+            if (!ptx::mbar_wait(&zfull[zb], (li >> 1) & 1, budget)) {
+                give_up();
+                break;
+            }
+            ptx::tc_fence_after();
+            const long long frame = (long long)((int)blockIdx.x + li * (int)gridDim.x) * 128 + r;
+            float2 *zo = prm.z_out + (size_t)(frame < prm.T ? frame : 0) * prm.K;
+            float zn2 = 0.f;
+            for (int c0 = 0; c0 < n1; c0 += 32) {
+                float v[32];
+                ptx::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(zb * kZBuf + c0), v);
+                if (frame < prm.T) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const int kk = (c0 + i) >> 1;
+                        if (kk < prm.K) {
+                            const float2 z = make_float2(v[i] * prm.inv_vscale, v[i + 1] * prm.inv_vscale);
+                            zo[kk] = z;
+                            zn2 = fmaf(z.x, z.x, fmaf(z.y, z.y, zn2));
+                        }
+                    }
+                }
+            }
+            if (prm.zn2_out && frame < prm.T) prm.zn2_out[frame] = zn2;
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&zempty[zb]);
+        }
+    } else if (warp == kTmaWarp) {
         if (lane == 0) {
-            int issued_stage = -1;
+            int issued = -1;
+            const int n_stages = my_tiles * stages_per_tile;
             for (int st = 0; st < n_stages; ++st) {
                 const int s = st & 1;
-                const uint32_t par = ((st >> 1) & 1) ^ 1;
                 if (*abort_flag) break;
-                if (!ptx::mbar_wait(&empty[s], par, budget)) {
+                if (!ptx::mbar_wait(&empty[s], ((st >> 1) & 1) ^ 1, budget)) {
                     give_up();
                     break;
                 }
-                const int g = st % prm.G;
+                const int sl = st % stages_per_tile;
+                const int g = sl % prm.G;
                 const int npg = min(kGroupPairs, prm.P - g * kGroupPairs);
-                const int steps = (npg + 1) >> 1;
-                const int atoms = (steps + 3) >> 2;
+                const int atoms = (((npg + 1) >> 1) + 3) >> 2;
                 ptx::mbar_arrive_expect_tx(&full_b[s], (uint32_t)(atoms * n1 * 128));
                 uint8_t *Bs = smem + off_b + s * b_stage;
                 for (int a = 0; a < atoms; ++a)
-                    ptx::tma_load_2d(Bs + a * n1 * 128, &tmap_v, &full_b[s], st * kGroupElems + a * kAtomElems, 0);
-                issued_stage = st;
+                    ptx::tma_load_2d(Bs + a * n1 * 128, &tmap_v, &full_b[s], sl * kGroupElems + a * kAtomElems, 0);
+                issued = st;
             }
-            // drain: wait for the last issued loads of both buffers to land
-            for (int st = max(0, issued_stage - 1); st <= issued_stage; ++st)
+            for (int st = max(0, issued - 1); st <= issued; ++st)
                 ptx::mbar_wait(&full_b[st & 1], (st >> 1) & 1, kDrainBudget);
         }
         __syncwarp();
-    } else if (warp == 9) {
-        // ---------------- MMA issuer
+    } else {  // kMmaWarp
         if (lane == 0) {
             const uint32_t idesc = ptx::idesc_f16(128, n1, BF16);
-            bool ok = true;
-            for (int st = 0; st < n_stages && ok; ++st) {
-                const int s = st & 1;
-                const uint32_t par = (st >> 1) & 1;
-                if (*abort_flag) { ok = false; break; }
-                if (!ptx::mbar_wait(&full_a[s], par, budget) || !ptx::mbar_wait(&full_b[s], par, budget)) {
+            int st = 0;
+            for (int li = 0; li < my_tiles; ++li) {
+                const int zb = li & 1;
+                if (*abort_flag) break;
+                if (!ptx::mbar_wait(&zempty[zb], ((li >> 1) & 1) ^ 1, budget)) {
                     give_up();
-                    ok = false;
                     break;
                 }
                 ptx::tc_fence_after();
-                const int g = st % prm.G;
-                const int npg = min(kGroupPairs, prm.P - g * kGroupPairs);
-                const int steps = (npg + 1) >> 1;
-                const uint32_t a_base = ptx::smem_u32(smem + s * a_stage);
-                const uint32_t b_base = ptx::smem_u32(smem + off_b + s * b_stage);
-                for (int k = 0; k < steps; ++k) {
-                    const uint32_t ao = (k >> 2) * kAtomBytes + (k & 3) * 32;
-                    const uint32_t bo = (k >> 2) * n1 * 128 + (k & 3) * 32;
-                    ptx::mma_f16(tmem, ptx::sw128_desc(a_base + ao), ptx::sw128_desc(b_base + bo), idesc,
-                                 (st > 0 || k > 0) ? 1u : 0u);
-                }
-                ptx::mma_commit(&empty[s]);
-            }
-            if (ok) {
-                ptx::mma_commit(g1_done);
-            } else {
-                ptx::mma_commit(drain);
-                ptx::mbar_wait(drain, 0, kDrainBudget);
-                drained = true;
-            }
-        }
-        __syncwarp();
-    }
-
-    // =============================================================== epilogue 1: Z
-    float *Zf = reinterpret_cast<float *>(smem + off_zf);
-    if (warp < 4) {
-        const int r = tid;  // TMEM lane = frame row
-        bool ok = !*abort_flag && ptx::mbar_wait(g1_done, 0, budget);
-        if (!ok && !*abort_flag) give_up();
-        if (ok) {
-            ptx::tc_fence_after();
-            const long long frame = t0 + r;
-            uint8_t *A2 = smem;  // GEMM2 A operand, k2_atoms atoms
-            for (int c0 = 0; c0 < n1; c0 += 32) {
-                float v[32];
-                ptx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-                for (int i = 0; i < 32; i += 2) {
-                    const int n = c0 + i;
-                    const float zr = v[i] * prm.inv_vscale, zi = v[i + 1] * prm.inv_vscale;
-                    const bool in = n < 2 * prm.K;
-                    Zf[r * zstride + n] = in ? zr : 0.f;
-                    Zf[r * zstride + n + 1] = in ? zi : 0.f;
-                    const uint32_t w = pack2<BF16>(in ? zr : 0.f, in ? zi : 0.f);
-                    const uint32_t off = (n >> 6) * kAtomBytes + ptx::sw128_offset(r, n & 63);
-                    *reinterpret_cast<uint32_t *>(A2 + off) = w;
-                    if (prm.z_out && in && frame < prm.T)
-                        prm.z_out[(size_t)frame * prm.K + (n >> 1)] = make_float2(zr, zi);
-                }
-            }
-            // zero the K padding of the GEMM2 A operand
-            for (int n = n1; n < prm.k2_atoms * kAtomElems; n += 2) {
-                const uint32_t off = (n >> 6) * kAtomBytes + ptx::sw128_offset(r, n & 63);
-                *reinterpret_cast<uint32_t *>(A2 + off) = 0u;
-            }
-            ptx::fence_proxy_async_smem();
-        }
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
-
-    // =============================================================== GEMM2 + top-8
-    float tv[kTop];
-    int ti[kTop];
-#pragma unroll
-    for (int i = 0; i < kTop; ++i) {
-        tv[i] = -__int_as_float(0x7f800000);
-        ti[i] = -1;
-    }
-    const bool scan = prm.do_scan && !*abort_flag;
-    if (scan) {
-        if (warp == 8) {
-            if (lane == 0) {
-                int issued = -1;
-                for (int j = 0; j < prm.nq; ++j) {
-                    const int u = j & 1;
-                    const uint32_t par = ((j >> 1) & 1) ^ 1;
-                    if (*abort_flag) break;
-                    if (!ptx::mbar_wait(&b2_empty[u], par, budget)) {
-                        give_up();
-                        break;
-                    }
-                    ptx::mbar_arrive_expect_tx(&b2_full[u], (uint32_t)(prm.k2_atoms * kAtomBytes));
-                    uint8_t *B2 = smem + off_b2 + u * prm.k2_atoms * kAtomBytes;
-                    for (int a = 0; a < prm.k2_atoms; ++a)
-                        ptx::tma_load_2d(B2 + a * kAtomBytes, &tmap_d, &b2_full[u], a * kAtomElems, j * 128);
-                    issued = j;
-                }
-                for (int j = max(0, issued - 1); j <= issued; ++j)
-                    ptx::mbar_wait(&b2_full[j & 1], (j >> 1) & 1, kDrainBudget);
-            }
-            __syncwarp();
-        } else if (warp == 9) {
-            if (lane == 0) {
-                const uint32_t idesc = ptx::idesc_f16(128, 128, BF16);
-                const int steps = prm.k2 >> 4;
                 bool ok = true;
-                for (int j = 0; j < prm.nq; ++j) {
-                    const int u = j & 1;
-                    const uint32_t par = (j >> 1) & 1;
-                    if (*abort_flag) { ok = false; break; }
-                    if (!ptx::mbar_wait(&b2_full[u], par, budget) || !ptx::mbar_wait(&t2_empty[u], par ^ 1, budget)) {
-                        give_up();
+                for (int sl = 0; sl < stages_per_tile; ++sl, ++st) {
+                    const int s = st & 1;
+                    const uint32_t par = (st >> 1) & 1;
+                    if (*abort_flag || !ptx::mbar_wait(&full_a[s], par, budget) ||
+                        !ptx::mbar_wait(&full_b[s], par, budget)) {
+                        if (!*abort_flag) give_up();
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t a_base = ptx::smem_u32(smem);
-                    const uint32_t b_base = ptx::smem_u32(smem + off_b2 + u * prm.k2_atoms * kAtomBytes);
+                    const int g = sl % prm.G;
+                    const int npg = min(kGroupPairs, prm.P - g * kGroupPairs);
+                    const int steps = (npg + 1) >> 1;
+                    const uint32_t a_base = ptx::smem_u32(smem + s * a_stage);
+                    const uint32_t b_base = ptx::smem_u32(smem + off_b + s * b_stage);
                     for (int k = 0; k < steps; ++k) {
-                        const uint32_t o = (k >> 2) * kAtomBytes + (k & 3) * 32;
-                        ptx::mma_f16(tmem + kTmemY + u * 128, ptx::sw128_desc(a_base + o), ptx::sw128_desc(b_base + o),
-                                     idesc, k > 0 ? 1u : 0u);
+                        const uint32_t ao = (k >> 2) * kAtomBytes + (k & 3) * 32;
+                        const uint32_t bo = (k >> 2) * n1 * 128 + (k & 3) * 32;
+                        ptx::mma_f16(tmem + zb * kZBuf, ptx::sw128_desc(a_base + ao), ptx::sw128_desc(b_base + bo),
+                                     idesc, (sl > 0 || k > 0) ? 1u : 0u);
                     }
-                    ptx::mma_commit(&b2_empty[u]);
-                    ptx::mma_commit(&t2_full[u]);
+                    ptx::mma_commit(&empty[s]);
                 }
-                (void)ok;
+                if (!ok) break;
+                ptx::mma_commit(&zfull[zb]);
             }
-            __syncwarp();
-        } else if (warp < 4) {
-            for (int j = 0; j < prm.nq; ++j) {
-                const int u = j & 1;
-                const uint32_t par = (j >> 1) & 1;
+            ptx::mma_commit(drain);  // completes once every MMA issued above is done
+            ptx::mbar_wait(drain, 0, kDrainBudget);
+        }
+        __syncwarp();
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ===================================================================== scan kernel
+struct ScanParams {
+    const float2 *Z;     // [T][K] complex64
+    const float *zn2;    // [T] ||Z||^2
+    int T, K, k2, k2_atoms, Qr, nq;
+    const int32_t *reps;
+    const float2 *Dc32;  // [Q][K] complex64
+    float tol_z;         // 2 * 2.1 u sqrt(L): candidate window per unit ||Z||
+    float tol_abs;       // 2 * 1e-6 L
+    int32_t *idx;
+    float *proj;
+};
+
+template <int BF16>
+__global__ void __launch_bounds__(kScanThreads, 2)
+    svd_scan_kernel(const __grid_constant__ CUtensorMap tmap_d, const ScanParams prm) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int k2_atoms = prm.k2_atoms;
+    const int b2_bytes = k2_atoms * kN2 * 128;          // one D tile
+    const int off_b2 = k2_atoms * kAtomBytes;
+    const int off_cand = off_b2 + kRing * b2_bytes;
+    const int off_cnt = off_cand + 128 * kCap * 4;
+    const int off_bar = off_cnt + 128 * 4;
+    int *cand = reinterpret_cast<int *>(smem + off_cand);
+    int *cnt_s = reinterpret_cast<int *>(smem + off_cnt);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + off_bar);
+    uint64_t *b2_full = bars + 0, *b2_empty = bars + kRing, *t2_full = bars + 2 * kRing, *t2_empty = bars + 3 * kRing;
+    uint64_t *drain = bars + 4 * kRing;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4 * kRing + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 4 * kRing + 2);
+    const long long budget = g_wait_budget;
+    const long long t0 = (long long)blockIdx.x * 128;
+    const int K = prm.K;
+
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            ptx::mbar_init(&b2_full[i], 1);
+            ptx::mbar_init(&b2_empty[i], 1);
+            ptx::mbar_init(&t2_full[i], 1);
+            ptx::mbar_init(&t2_empty[i], 128);
+        }
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 4 && lane == 0) ptx::prefetch_tmap(&tmap_d);
+    if (warp == 5) {
+        ptx::tmem_alloc(tmem_slot, kRing * kN2);
+        ptx::tmem_relinquish();
+    }
+    __syncthreads();
+    // A operand: Z rounded to FP16/BF16, [128 frames][k2] in the 128-byte swizzle layout
+    for (int e = tid; e < 128 * (k2_atoms * kAtomElems / 2); e += kScanThreads) {
+        const int r = e / (k2_atoms * kAtomElems / 2), kk = e % (k2_atoms * kAtomElems / 2);
+        float2 z = make_float2(0.f, 0.f);
+        if (kk < K && t0 + r < prm.T) z = prm.Z[(size_t)(t0 + r) * K + kk];
+        const int n = 2 * kk;
+        *reinterpret_cast<uint32_t *>(smem + (n >> 6) * kAtomBytes + ptx::sw128_offset(r, n & 63)) = pack2<BF16>(z.x, z.y);
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        atomicOr(&g_status, 1);
+    };
+    const int n_jobs = 2 * prm.nq;  // pass 0 then pass 1 over the class tiles
+
+    if (warp < 4) {
+        const int r = tid;  // TMEM lane = frame row
+        const long long frame = t0 + r;
+        const float win = prm.tol_z * sqrtf(frame < prm.T ? prm.zn2[frame] : 0.f) + prm.tol_abs;
+        float m = -__int_as_float(0x7f800000), thr = 0.f;
+        int cnt = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            const int u = j % kRing;
+            const int tile = j % prm.nq, pass = j / prm.nq;
+            if (j == prm.nq) thr = m - win;
+            if (*abort_flag) break;
+            if (!ptx::mbar_wait(&t2_full[u], (j / kRing) & 1, budget)) {
+                give_up();
+                break;
+            }
+            ptx::tc_fence_after();
+            {
+                float v[kN2];
+                ptx::tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * kN2), v);
+                const int qb = tile * kN2;
+                if (pass == 0) {
+#pragma unroll
+                    for (int i = 0; i < kN2; ++i)
+                        if (qb + i < prm.Qr) m = fmaxf(m, v[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kN2; ++i) {
+                        if (v[i] >= thr && qb + i < prm.Qr) {
+                            if (cnt < kCap) cand[r * kCap + cnt] = qb + i;
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&t2_empty[u]);
+        }
+        cnt_s[r] = (frame < prm.T && m == m && thr == thr) ? cnt : 0;
+    } else if (warp == 4) {
+        if (lane == 0) {
+            int issued = -1;
+            for (int j = 0; j < n_jobs; ++j) {
+                const int u = j % kRing;
                 if (*abort_flag) break;
-                if (!ptx::mbar_wait(&t2_full[u], par, budget)) {
+                if (!ptx::mbar_wait(&b2_empty[u], ((j / kRing) & 1) ^ 1, budget)) {
+                    give_up();
+                    break;
+                }
+                ptx::mbar_arrive_expect_tx(&b2_full[u], (uint32_t)b2_bytes);
+                uint8_t *B2 = smem + off_b2 + u * b2_bytes;
+                const int tile = j % prm.nq;
+                for (int a = 0; a < k2_atoms; ++a)
+                    ptx::tma_load_2d(B2 + a * kN2 * 128, &tmap_d, &b2_full[u], a * kAtomElems, tile * kN2);
+                issued = j;
+            }
+            for (int j = max(0, issued - kRing + 1); j <= issued; ++j)
+                ptx::mbar_wait(&b2_full[j % kRing], (j / kRing) & 1, kDrainBudget);
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = ptx::idesc_f16(128, kN2, BF16);
+            const int steps = prm.k2 >> 4;
+            const uint32_t a_base = ptx::smem_u32(smem);
+            for (int j = 0; j < n_jobs; ++j) {
+                const int u = j % kRing;
+                const uint32_t par = (j / kRing) & 1;
+                if (*abort_flag) break;
+                if (!ptx::mbar_wait(&b2_full[u], par, budget) || !ptx::mbar_wait(&t2_empty[u], par ^ 1, budget)) {
                     give_up();
                     break;
                 }
                 ptx::tc_fence_after();
-#pragma unroll 1
-                for (int c0 = 0; c0 < 128; c0 += 32) {
-                    float v[32];
-                    ptx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kTmemY + u * 128 + c0), v);
-                    const int qb = j * 128 + c0;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float y = v[i];
-                        if (y > tv[kTop - 1] && qb + i < prm.Q) {
-                            tv[kTop - 1] = y;
-                            ti[kTop - 1] = qb + i;
-#pragma unroll
-                            for (int x = kTop - 1; x > 0; --x) {
-                                if (tv[x] > tv[x - 1]) {
-                                    const float fv = tv[x]; tv[x] = tv[x - 1]; tv[x - 1] = fv;
-                                    const int iv = ti[x]; ti[x] = ti[x - 1]; ti[x - 1] = iv;
-                                }
-                            }
-                        }
-                    }
+                const uint32_t b_base = ptx::smem_u32(smem + off_b2 + u * b2_bytes);
+                for (int k = 0; k < steps; ++k) {
+                    const uint32_t ao = (k >> 2) * kAtomBytes + (k & 3) * 32;
+                    const uint32_t bo = (k >> 2) * kN2 * 128 + (k & 3) * 32;
+                    ptx::mma_f16(tmem + u * kN2, ptx::sw128_desc(a_base + ao), ptx::sw128_desc(b_base + bo), idesc,
+                                 k > 0 ? 1u : 0u);
                 }
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(&t2_empty[u]);
+                ptx::mma_commit(&b2_empty[u]);
+                ptx::mma_commit(&t2_full[u]);
             }
+            ptx::mma_commit(drain);
+            ptx::mbar_wait(drain, 0, kDrainBudget);
         }
+        __syncwarp();
     }
     __syncthreads();
 
-    // =============================================================== rescoring
-    if (scan && warp < 4 && !*abort_flag) {
-        const int r = tid;
-        const long long frame = t0 + r;
-        if (frame < prm.T) {
+    // -------- rescoring in FP32: a warp takes two frames at a time (16 lanes each); lane
+    // (c, part) sums the terms k = part, part + 4, ... of candidate c, 4 candidates per round.
+    if (!*abort_flag) {
+        const int h = lane >> 4, c4 = (lane >> 2) & 3, part = lane & 3;
+        for (int r0 = 2 * warp; r0 < 128; r0 += 2 * (kScanThreads / 32)) {
+            const int r = r0 + h;
+            const long long frame = t0 + r;
+            const bool live = frame < prm.T;
+            const int n = live ? cnt_s[r] : 0;
+            const int total = n <= kCap ? n : prm.Qr;   // n > kCap: every class
+            const float2 *zr = prm.Z + (size_t)(live ? frame : 0) * K;
             float best = 0.f;
             int bq = -1;
-#pragma unroll
-            for (int c = 0; c < kTop; ++c) {
-                const int q = ti[c];
-                if (q < 0) continue;
-                const float2 *dq = prm.Dc32 + (size_t)q * prm.K;
+            const int tmax = max(total, __shfl_xor_sync(0xffffffffu, total, 16));
+            for (int base = 0; base < tmax; base += 4) {
+                const int c = base + c4;
+                int q = -1;
+                if (c < total) q = prm.reps[n <= kCap ? cand[r * kCap + c] : c];
                 float acc = 0.f;
-                for (int k = 0; k < prm.K; ++k) {
-                    const float2 d = __ldg(dq + k);
-                    acc = fmaf(d.x, Zf[r * zstride + 2 * k], acc);
-                    acc = fmaf(-d.y, Zf[r * zstride + 2 * k + 1], acc);
+                if (q >= 0) {
+                    const float2 *dq = prm.Dc32 + (size_t)q * K;
+#pragma unroll 6
+                    for (int kk = part; kk < K; kk += 4) {
+                        const float2 d = __ldg(dq + kk), z = __ldg(zr + kk);
+                        acc = fmaf(d.x, z.x, acc);
+                        acc = fmaf(-d.y, z.y, acc);
+                    }
                 }
-                if (bq < 0 || acc > best || (acc == best && q < bq)) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (q >= 0 && (bq < 0 || acc > best || (acc == best && q < bq))) {
                     best = acc;
                     bq = q;
                 }
             }
-            prm.idx[frame] = bq;
-            if (prm.proj) prm.proj[frame] = bq < 0 ? __int_as_float(0x7fc00000) : best;
+            // best over the 4 candidate groups of this half-warp
+#pragma unroll
+            for (int o = 4; o < 16; o <<= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+                const bool take = (bq < 0) || (oq >= 0 && (ov > best || (ov == best && oq < bq)));
+                if (take) {
+                    best = ov;
+                    bq = oq;
+                }
+            }
+            if ((lane & 15) == 0 && live) {
+                prm.idx[frame] = bq;
+                if (prm.proj) prm.proj[frame] = bq < 0 ? __int_as_float(0x7fc00000) : best;
+            }
         }
-    }
-
-    if (warp == 9 && lane == 0 && !drained) {
-        ptx::mma_commit(drain);  // completes once every MMA this thread issued is done
-        ptx::mbar_wait(drain, 0, kDrainBudget);
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 9) {
+    if (warp == 5) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem, kTmemCols);
+        ptx::tmem_dealloc(tmem, kRing * kN2);
     }
 }
 
@@ -556,7 +654,7 @@ struct TcMaps {
 
 int tc_prepare(sp_basis *b) {
     const sp_steering *st = b->st;
-    const int K = b->K, P = st->P, B = st->B, Q = st->Q, L = st->L;
+    const int K = b->K, P = st->P, B = st->B, L = st->L;
     TcLayout t = make_tc_layout(P, B, K);
     b->tc = t;
     if (t.n1 > kMaxN1 || st->M > 16) {
@@ -588,12 +686,15 @@ int tc_prepare(sp_basis *b) {
                 }
             }
     const int dcols = t.k2_atoms * kAtomElems;
-    std::vector<float> df((size_t)Q * dcols, 0.f);
-    for (int q = 0; q < Q; ++q)
+    const int Qr = (int)st->reps.size();
+    std::vector<float> df((size_t)Qr * dcols, 0.f);
+    for (int r = 0; r < Qr; ++r) {
+        const size_t q = (size_t)st->reps[r];
         for (int kk = 0; kk < K; ++kk) {
-            df[(size_t)q * dcols + 2 * kk] = (float)b->D[((size_t)q * K + kk) * 2];
-            df[(size_t)q * dcols + 2 * kk + 1] = (float)-b->D[((size_t)q * K + kk) * 2 + 1];
+            df[(size_t)r * dcols + 2 * kk] = (float)b->D[(q * K + kk) * 2];
+            df[(size_t)r * dcols + 2 * kk + 1] = (float)-b->D[(q * K + kk) * 2 + 1];
         }
+    }
     TcMaps *maps = new TcMaps();
     for (int prec = 0; prec < 2; ++prec) {
         std::vector<uint16_t> hv(nv), hd(df.size());
@@ -610,7 +711,7 @@ int tc_prepare(sp_basis *b) {
         SP_CUDA(cudaMemcpy(b->Vtc[prec].p, hv.data(), nv * 2, cudaMemcpyHostToDevice));
         SP_CUDA(cudaMemcpy(b->Dtc[prec].p, hd.data(), hd.size() * 2, cudaMemcpyHostToDevice));
         int rc = encode_2d(&maps->v[prec], b->Vtc[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.n1);
-        if (rc == SP_OK) rc = encode_2d(&maps->d[prec], b->Dtc[prec].p, prec, dcols, Q, kAtomElems, 128);
+        if (rc == SP_OK) rc = encode_2d(&maps->d[prec], b->Dtc[prec].p, prec, dcols, Qr, kAtomElems, kN2);
         if (rc != SP_OK) {
             delete maps;
             return rc;
@@ -625,16 +726,26 @@ void tc_release(sp_basis *b) {
     b->tc_maps = nullptr;
 }
 
-int launch_svd_tc(const sp_basis *b, const void *frames, int T, int prec, int32_t *idx, float *proj,
-                  void *z_out, cudaStream_t s) {
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
+                    cudaStream_t s) {
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
              "tensor-core path supports 2K <= 144 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
-    const SmemPlan plan = make_plan(t);
-    TcParams p;
+    ProjParams p;
     p.frames = (const float2 *)frames;
     p.T = T;
     p.M = b->st->M;
@@ -644,32 +755,66 @@ int launch_svd_tc(const sp_basis *b, const void *frames, int T, int prec, int32_
     p.n_chunks = t.n_chunks;
     p.n1 = t.n1;
     p.K = b->K;
-    p.Q = b->st->Q;
+    p.n_tiles = (int)(((long long)T + 127) / 128);
+    p.inv_vscale = 1.f / b->v_scale;
+    p.z_out = (float2 *)z_out;
+    p.zn2_out = zn2_out;
+    const int smem = 2 * 3 * kAtomBytes + 2 * 3 * t.n1 * 128 + 128 + 1024;
+    SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
+    // variants: exactly 7 microphones (the Table 2 arrays), up to 8, up to 16
+    const int which = bf * 3 + (p.M == 7 ? 0 : p.M <= 8 ? 1 : 2);
+    void (*const kerns[6])(CUtensorMap, ProjParams) = {
+        svd_proj_kernel<0, 7, true, 2>, svd_proj_kernel<0, 8, false, 2>, svd_proj_kernel<0, 16, false, 1>,
+        svd_proj_kernel<1, 7, true, 2>, svd_proj_kernel<1, 8, false, 2>, svd_proj_kernel<1, 16, false, 1>};
+    auto kern = kerns[which];
+    static bool attr[6] = {false, false, false, false, false, false};
+    if (!attr[which]) {
+        SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+        attr[which] = true;
+    }
+    // at least 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM
+    const int smem_launch = std::max(smem, 120 * 1024);
+    const int grid = std::min(p.n_tiles, num_sms());
+    kern<<<grid, kProjThreads, smem_launch, s>>>(maps->v[bf], p);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
+                    float *proj, cudaStream_t s) {
+    if (T == 0) return SP_OK;
+    const TcLayout &t = b->tc;
+    SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
+             "tensor-core path supports 2K <= 144 and M <= 16 (use SP_PREC_FP32)");
+    const int bf = prec == SP_PREC_BF16 ? 1 : 0;
+    const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
+    ScanParams p;
+    p.Z = (const float2 *)Z;
+    p.zn2 = zn2;
+    p.T = T;
+    p.K = b->K;
     p.k2 = t.k2;
     p.k2_atoms = t.k2_atoms;
-    p.nq = (p.Q + 127) / 128;
-    p.inv_vscale = 1.f / b->v_scale;
-    p.do_scan = idx != nullptr;
+    p.Qr = (int)b->st->reps.size();
+    p.nq = (p.Qr + kN2 - 1) / kN2;
+    p.reps = b->st->d_reps.as<int32_t>();
     p.Dc32 = b->Dc32.as<float2>();
+    const double u = bf ? std::ldexp(1.0, -8) : std::ldexp(1.0, -11);  // unit roundoff
+    const double L = (double)b->st->L;
+    p.tol_z = (float)(2.0 * 2.1 * u * std::sqrt(L));
+    p.tol_abs = (float)(2.0 * 1e-6 * L);
     p.idx = idx;
     p.proj = proj;
-    p.z_out = (float2 *)z_out;
-    static bool attr_set[2] = {false, false};
-    if (bf) {
-        if (!attr_set[1]) {
-            SP_CUDA(cudaFuncSetAttribute(svd_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-            attr_set[1] = true;
-        }
-    } else if (!attr_set[0]) {
-        SP_CUDA(cudaFuncSetAttribute(svd_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-        attr_set[0] = true;
+    const int smem = t.k2_atoms * kAtomBytes + kRing * t.k2_atoms * kN2 * 128 + 128 * kCap * 4 + 128 * 4 +
+                     (4 * kRing + 3) * 8 + 1024;
+    auto kern = bf ? svd_scan_kernel<1> : svd_scan_kernel<0>;
+    static bool attr[2] = {false, false};
+    if (!attr[bf]) {
+        SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+        attr[bf] = true;
     }
-    SP_CHECK(plan.total <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
     const unsigned grid = (unsigned)(((long long)T + 127) / 128);
-    if (bf)
-        svd_tc_kernel<1><<<grid, kThreads, plan.total, s>>>(maps->v[1], maps->d[1], p);
-    else
-        svd_tc_kernel<0><<<grid, kThreads, plan.total, s>>>(maps->v[0], maps->d[0], p);
+    kern<<<grid, kScanThreads, smem, s>>>(maps->d[bf], p);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -47,13 +47,17 @@ CONFIGS = [("linear_q642", 100), ("planar_q2562", 777)]
 
 
 def _agree(d, idx, Y, margin_tol=1e-4, min_agree=0.995):
+    """Class-level agreement: identical wherever the oracle's top-2 margin exceeds margin_tol,
+    and >= min_agree over all frames (checked when there are >= 400 frames: below that a
+    single near-tie frame is more than 0.25 %)."""
     cls = d["cls"]
     ref, _ = O.argmax_lowest(Y)
     m = O.top2_margin(Y, cls)
     same = cls[idx] == cls[ref]
     big = m > margin_tol
     assert np.all(same[big]), f"{np.sum(~same[big])} frames with margin > {margin_tol} disagree"
-    assert np.mean(same) >= min_agree, np.mean(same)
+    if len(idx) >= 400:
+        assert np.mean(same) >= min_agree, np.mean(same)
     return np.mean(same)
 
 
@@ -71,6 +75,12 @@ def test_tau_bit_exact_random_geometry():
     dirs = rng.standard_normal((1000, 3)) * rng.uniform(0.1, 10, size=(1000, 1))
     st = sp.build_steering(mic, dirs, 44100.0, 340.5, 256)
     assert np.array_equal(st.tau(), O.tdoa_farfield(mic, dirs, 44100.0, 340.5))
+
+
+@pytest.mark.parametrize("name,T", CONFIGS)
+def test_direction_classes_match_oracle(name, T):
+    d = _setup(name, T)
+    assert np.array_equal(d["st"].classes(), d["cls"])
 
 
 @pytest.mark.parametrize("name,T", CONFIGS)
@@ -141,6 +151,7 @@ def test_localize_svd_exhaustive(name, T, prec, tol):
     sp.check_status()
     idx = idx.cpu().numpy()
     _agree(d, idx, d["Ysvd"])
+    assert np.all(d["cls"][idx] == idx)           # the lowest index of the winning class
     assert np.max(np.abs(proj.cpu().numpy() - d["Ysvd"][np.arange(T), idx])) <= tol * d["L"]
     sref = O.score_row(d["tau"], idx, d["X"], d["wl"]["N"])       # Algorithm 1 online step 4
     assert np.max(np.abs(score.cpu().numpy() - sref)) <= 2e-5 * d["L"]
@@ -164,16 +175,25 @@ def test_localize_kdtree(name, T, prec):
     dsec = np.where(cls[None, :] == cls[nn][:, None], np.inf, dist).min(axis=1)
     clear = dsec - d2 > 1e-5
     assert np.all(cls[idx[clear]] == cls[nn[clear]])
+    assert np.all(cls[idx] == idx)                 # the tree holds one point per class
     # against the oracle's own normalised search (Eq. 15) on its FP64 query
-    ref, _ = O.nn_brute(d["ob"]["Dhat"], d["Z"])
-    assert np.mean(cls[idx] == cls[ref]) >= 0.995
+    Dh = d["ob"]["Dhat"]
+    ref, rd2 = O.nn_brute(Dh, d["Z"])
+    Zo = np.conj(d["Z"] / np.linalg.norm(d["Z"], axis=1, keepdims=True))
+    od = np.sum(np.abs(Dh[None, :, :] - Zo[:, None, :]) ** 2, axis=2)
+    osec = np.where(cls[None, :] == cls[ref][:, None], np.inf, od).min(axis=1)
+    big = (osec - rd2) > 1e-4
+    assert np.all(cls[idx[big]] == cls[ref[big]])
+    if T >= 400:
+        assert np.mean(cls[idx] == cls[ref]) >= 0.995
     assert np.max(np.abs(proj.cpu().numpy() - (1 - d2 / 2))) < 1e-4
 
 
 def test_tree_shape():
     d = _setup("planar_q2562", 777)
     info = d["b"].kdtree_info()
-    assert info["leaf_size"] == 32 and info["n_nodes"] >= 2 * (2562 // 32) - 1
+    n_classes = len(np.unique(d["cls"]))
+    assert info["leaf_size"] == 32 and info["n_nodes"] >= 2 * (n_classes // 32) - 1
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
