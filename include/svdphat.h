@@ -190,6 +190,30 @@ int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode 
                      sp_prec prec, int32_t *idx_host, float *score_host,
                      float *proj_score_host, int chunk_frames, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * sp_localize without any allocation (the paper has no counterpart; this is a deployment
+ * aid).  Some callers cannot call cudaMalloc on their processing path: real-time audio
+ * callbacks and plugin hosts, where the allocator can block on driver locks and miss the
+ * audio deadline, and deployments whose device memory budget is fixed at start-up.  This
+ * entry point runs the same kernels as sp_localize with SP_MODE_SVD_EXHAUSTIVE, but keeps
+ * its scratch (the Z vectors and their norms) in an 8 MiB array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * prec: SP_PREC_FP16 or SP_PREC_BF16 (SP_ENOTIMPL otherwise).  A call needs
+ * T * (8 K + 4) bytes of that scratch (K from sp_svd_reduce; at K = 48 that is up to
+ * 21,000 frames per call); larger T is rejected with SP_EINVAL before any work is queued.
+ * idx_dev, score_dev, proj_score_dev: as for sp_localize.  The caller still provides the
+ * frames and all outputs.
+ *
+ * The first call on a device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.  The call itself
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).  Every call
+ * on a device shares the one array, which keeps the last call's contents; nothing in it
+ * needs to start at zero.  Calls whose work overlaps on the GPU (other streams, other
+ * threads) race on the array: serialise them. */
+int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
+                        int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream);
+
 /* Synchronise stream and report a device-side failure recorded since the last call
  * (SP_ETIMEOUT if a bounded wait gave up), clearing it. */
 int sp_check_status(void *stream);

@@ -55,6 +55,7 @@ _SIGS = {
     "sp_localize_srp": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "sp_localize_host": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
                           _vp], ctypes.c_int),
+    "sp_localize_noalloc": ([_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
     "sp_check_status": ([_vp], ctypes.c_int),
     "sp_set_wait_budget": ([ctypes.c_longlong], ctypes.c_int),
 }
@@ -280,6 +281,23 @@ def localize_host(basis: Basis, frames_host, mode="svd_exhaustive", prec="fp16",
     _check("sp_localize_host", lib().sp_localize_host(basis.handle, _ptr(frames_host), T, _mode(mode), _prec(prec),
                                                       _ptr(idx), _ptr(sc), _ptr(pj), int(chunk_frames),
                                                       _stream()))
+    return idx, sc, pj
+
+
+def localize_noalloc(basis: Basis, frames, prec="fp16", score=True, proj=True, out=None):
+    """sp_localize_noalloc: exhaustive FP16/BF16 localisation whose scratch lives in a fixed
+    array inside the library (no allocation in the call); T is bounded by that array."""
+    import torch
+    _frames(frames, basis.steering)
+    T = frames.shape[0]
+    if out is None:
+        idx = torch.empty(T, dtype=torch.int32, device=frames.device)
+        sc = torch.empty(T, dtype=torch.float32, device=frames.device) if score else None
+        pj = torch.empty(T, dtype=torch.float32, device=frames.device) if proj else None
+    else:
+        idx, sc, pj = out
+    _check("sp_localize_noalloc", lib().sp_localize_noalloc(basis.handle, _ptr(frames), T, _prec(prec), _ptr(idx),
+                                                            _ptr(sc), _ptr(pj), _stream()))
     return idx, sc, pj
 
 
