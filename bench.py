@@ -4,8 +4,8 @@ Workload: 7-mic planar array (centre + 6 mics on a 5 cm circle), fs 16 kHz, N = 
 B = 257 bins), Q = 2562 icosphere directions, K from delta = 1e-5 (K = 48), 65,536 frames
 per step with one white-noise plane-wave source per frame at SNR U(-5, 20) dB (synthetic).
 A step is one pass of Algorithm 1's online path over the batch: PHAT -> Z = V^H X ->
-exhaustive Re{D Z} argmax (FP16 tensor cores + FP32 top-8 rescoring) -> Y_qbar from the row
-of W (online step 4).  The STFT batch (943 MB) is larger than L2, so no flush is needed.
+exhaustive Re{D Z} argmax (FP16 tensor cores, then FP32 rescoring of every class within the
+FP16 rounding bound of the best) -> Y_qbar from the row of W (online step 4).  The STFT batch (943 MB) is larger than L2, so no flush is needed.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec fp16|bf16]
 Under torchrun each rank localises its own 65,536 frames (weak scaling, no collective on the
@@ -14,6 +14,7 @@ data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -32,6 +33,11 @@ METRIC = "localized frames/s at >=99.5% argmax agreement vs FP64 oracle"
 UNIT = "frames/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes read + written per frame by svd_proj_kernel, from one ncu capture of this
+# version of the kernel on 19,456 frames of the same workload (311.2 MB / 19,456), scaled to
+# a launch by the frame count (traffic grows in proportion to frames).  Set to None when the
+# kernel changes until it is captured again.
+TRAFFIC_PER_FRAME = 15994.0
 
 
 def _peaks():
@@ -185,6 +191,12 @@ def main():
     import paper_1811_11785_gb300 as sp
     from paper_1811_11785_gb300 import inputs as I
 
+    def lib_project(b, frames, prec, zout):
+        rc = sp.lib().sp_project(b.handle, ctypes.c_void_p(frames.data_ptr()), frames.shape[0], sp.PREC[prec],
+                                 ctypes.c_void_p(zout.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, sp.lib().sp_last_error()
+
     T = args.frames
     wl = I.workload(WORKLOAD, T=T, seed_offset=rank)
     st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"], materialize_w=True)
@@ -224,17 +236,25 @@ def main():
     clk = clocks.stop()
     sp.check_status()
 
-    # dominant kernel alone (the fused PHAT -> GEMM1 -> GEMM2/top-8 -> rescoring kernel)
+    # per-kernel durations on the launching stream: the dominant kernel (fused PHAT + GEMM1,
+    # svd_proj_kernel) alone through sp_project, then + the scan, then + online step 4
+    zbuf = torch.empty((T, b.K), dtype=torch.complex64, device="cuda")
     kout = (idx, None, proj)
-    for _ in range(3):
-        sp.localize(b, frames, "svd_exhaustive", args.prec, out=kout)
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for _ in range(args.steps):
-        sp.localize(b, frames, "svd_exhaustive", args.prec, out=kout)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    k_ms = k0.elapsed_time(k1) / args.steps
+
+    def avg_ms(fn, n):
+        for _ in range(3):
+            fn()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / n
+
+    k_ms = avg_ms(lambda: lib_project(b, frames, args.prec, zbuf), args.steps)
+    scan_ms = avg_ms(lambda: sp.localize(b, frames, "svd_exhaustive", args.prec, out=kout), args.steps) - k_ms
+    step4_ms = ms / args.steps - k_ms - scan_ms
 
     # end to end through the host-buffer entry point: H2D of the frames and D2H of the results
     hout = (torch.empty(T, dtype=torch.int32).pin_memory(), torch.empty(T, dtype=torch.float32).pin_memory(),
@@ -279,9 +299,9 @@ def main():
             extras["svd_kdtree_fp16_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_kdtree", "fp16"), 3)
 
         peak, peak_kind = _peaks()
-        per_frame_bytes = st.M * st.B * 8 + 4 + 4          # STFT read + idx + proj written
+        frame_bytes = st.M * st.B * 8                       # the STFT of one frame
+        per_frame_bytes = frame_bytes                       # algorithmic bytes of the dominant kernel
         achieved = per_frame_bytes * T / (k_ms / 1000) / 1e9
-        frame_bytes = st.M * st.B * 8
         line = {
             "metric": METRIC, "value": T * ws * args.steps / (ms / 1000), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -290,14 +310,16 @@ def main():
             "config": {"workload": f"{WORKLOAD}: 7-mic planar array, Q=2562, N=512, K={b.K}, "
                                    f"{T} frames/step/GPU, SNR U(-5,20) dB",
                        "frames_per_step": T, "Q": st.Q, "M": st.M, "N": st.N, "K": b.K,
-                       "mode": "svd_exhaustive + top-8 FP32 rescoring + online step 4",
+                       "mode": "svd_exhaustive (FP16/BF16 scan + FP32 rescoring of every class within the "
+                               "rounding bound) + online step 4",
                        "l2": "inputs (943 MB STFT) larger than L2; no flush"},
             "agreement_vs_oracle": agree, "agreement_sample_frames": int(len(sel)),
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "svd_tc_kernel",
-                         "kernel_ms": k_ms, "peak_source": peak_kind,
+                         "frac": achieved / peak, "traffic": TRAFFIC_PER_FRAME and TRAFFIC_PER_FRAME * T,
+                         "kernel": "svd_proj_kernel", "kernel_ms": k_ms, "peak_source": peak_kind,
                          "algorithmic_bytes_per_frame": per_frame_bytes},
+            "kernel_ms": {"svd_proj_kernel": k_ms, "svd_scan_kernel": scan_ms, "score_row_kernel": step4_ms},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                              "sample": "2048 frames of the same workload (PHAT, Z = V^H X, Re{D Z} argmax, "
                                        "online step 4 in FP64 numpy)"},

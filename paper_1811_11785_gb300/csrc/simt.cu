@@ -307,13 +307,15 @@ int launch_project_f32(const sp_basis *b, const void *X, int T, void *Z, cudaStr
 //     sum_{i<j} Re{y_i conj(y_j)} = (|sum_m y_m|^2 - sum_m |y_m|^2) / 2
 // per bin: O(M) work per bin instead of O(P).  One warp per frame, lane l takes bins
 // l, l + 32, ...; the phasor of mic m at bin k is advanced by exp(-2 pi i 32 d_m / N) from
-// one bin of the lane to the next (one sincospi pair per mic and lane, fresh per frame).
-// d_m is formed in FP64 once per mic by lane m and broadcast.
-template <int MMAX>
+// one bin of the lane to the next.  Lane m forms d_m in FP64 (d_m / N split into two floats
+// so that k d_m / N is exact to ~1e-9 turns) and the 32-bin step phasor; both are broadcast.
+// MMAX: bound on the microphone count (EXACT: M == MMAX at compile time).
+template <int MMAX, bool EXACT>
 __global__ void __launch_bounds__(256)
-    score_row_kernel(const float2 *__restrict__ frames, int T, int M, int B, double inv_n,
+    score_row_kernel(const float2 *__restrict__ frames, int T, int M_rt, int B, double inv_n,
                      const double *__restrict__ unit, const double *__restrict__ mic, double g,
                      const int32_t *__restrict__ idx, float *__restrict__ score) {
+    const int M = EXACT ? MMAX : M_rt;
     const int lane = threadIdx.x & 31;
     const long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= T) return;
@@ -322,36 +324,34 @@ __global__ void __launch_bounds__(256)
         if (lane == 0) score[t] = __int_as_float(0x7fc00000);
         return;
     }
-    // lane m < M: advance of mic m in turns per bin, e = d_m / N (FP64), split hi + lo
-    float my_hi = 0.f, my_lo = 0.f;
+    float my_hi = 0.f, my_lo = 0.f, my_sc = 1.f, my_ss = 0.f;
     if (lane < M) {
         const double d = g * ((mic[3 * lane] * unit[3 * q] + mic[3 * lane + 1] * unit[3 * q + 1]) +
                               mic[3 * lane + 2] * unit[3 * q + 2]);
         const double e = d * inv_n;
         my_hi = (float)e;
         my_lo = (float)(e - (double)my_hi);
+        const float p1 = 32.f * my_hi;
+        const float r1 = (p1 - rintf(p1)) + 32.f * my_lo;
+        sincospif(-2.f * r1, &my_ss, &my_sc);
     }
     const float2 *fr = frames + (size_t)t * M * B;
-    float acc = 0.f;
     float2 ph[MMAX], stp[MMAX];
 #pragma unroll
     for (int m = 0; m < MMAX; ++m) {
         const float ehi = __shfl_sync(0xffffffffu, my_hi, m);
         const float elo = __shfl_sync(0xffffffffu, my_lo, m);
+        stp[m] = make_float2(__shfl_sync(0xffffffffu, my_sc, m), __shfl_sync(0xffffffffu, my_ss, m));
         if (m < M) {
-            // phase of bin `lane` and of a 32-bin step, reduced to [-1/2, 1/2] turns
             const float kf = (float)lane;
-            float p0 = kf * ehi;
+            const float p0 = kf * ehi;
             const float r0 = (p0 - rintf(p0)) + fmaf(kf, elo, fmaf(kf, ehi, -p0));
-            float p1 = 32.f * ehi;
-            const float r1 = (p1 - rintf(p1)) + 32.f * elo;
             float s, c;
             sincospif(-2.f * r0, &s, &c);
             ph[m] = make_float2(c, s);
-            sincospif(-2.f * r1, &s, &c);
-            stp[m] = make_float2(c, s);
         }
     }
+    float acc = 0.f;
     // three bins per lane per round: 3 * M independent loads in flight
     for (int k0 = lane; k0 < B; k0 += 96) {
         float2 v[3][MMAX];
@@ -369,14 +369,12 @@ __global__ void __launch_bounds__(256)
                     const float2 x = v[u][m];
                     const float mag2 = x.x * x.x + x.y * x.y;
                     const float2 w = ph[m];
-                    if (mag2 >= kZeroMag2) {
-                        const float r = rsqrtf(mag2);
-                        const float xr = x.x * r, xi = x.y * r;
-                        const float yr = xr * w.x - xi * w.y, yi = xr * w.y + xi * w.x;
-                        sr += yr;
-                        si += yi;
-                        en += yr * yr + yi * yi;
-                    }
+                    const float r = mag2 >= kZeroMag2 ? rsqrtf(mag2) : 0.f;
+                    const float xr = x.x * r, xi = x.y * r;
+                    const float yr = xr * w.x - xi * w.y, yi = xr * w.y + xi * w.x;
+                    sr += yr;
+                    si += yi;
+                    en += yr * yr + yi * yi;
                     const float2 st = stp[m];
                     ph[m] = make_float2(w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x);
                 }
@@ -394,7 +392,7 @@ int launch_score_row(const sp_steering *st, const void *frames, int T, const int
     if (T == 0) return SP_OK;
     SP_CHECK(st->M <= 16, SP_ENOTIMPL, "online step 4 supports M <= 16");
     const long long blocks = ((long long)T + 7) / 8;
-    auto kern = st->M <= 8 ? score_row_kernel<8> : score_row_kernel<16>;
+    auto kern = st->M == 7 ? score_row_kernel<7, true> : st->M <= 8 ? score_row_kernel<8, false> : score_row_kernel<16, false>;
     kern<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, 1.0 / (double)st->N,
                                           st->d_dirs.as<double>(), st->d_mic.as<double>(), st->fs / st->c, idx, score);
     SP_CUDA(cudaGetLastError());

@@ -447,12 +447,28 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     }
     __syncthreads();
     // A operand: Z rounded to FP16/BF16, [128 frames][k2] in the 128-byte swizzle layout
-    for (int e = tid; e < 128 * (k2_atoms * kAtomElems / 2); e += kScanThreads) {
-        const int r = e / (k2_atoms * kAtomElems / 2), kk = e % (k2_atoms * kAtomElems / 2);
-        float2 z = make_float2(0.f, 0.f);
-        if (kk < K && t0 + r < prm.T) z = prm.Z[(size_t)(t0 + r) * K + kk];
-        const int n = 2 * kk;
-        *reinterpret_cast<uint32_t *>(smem + (n >> 6) * kAtomBytes + ptx::sw128_offset(r, n & 63)) = pack2<BF16>(z.x, z.y);
+    // (8 loads in flight per thread)
+    {
+        const int per_row = k2_atoms * kAtomElems / 2;
+        const int n_el = 128 * per_row;
+        for (int e0 = tid; e0 < n_el; e0 += 8 * kScanThreads) {
+            float2 z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * kScanThreads;
+                const int r = e / per_row, kk = e % per_row;
+                z[u] = (e < n_el && kk < K && t0 + r < prm.T) ? prm.Z[(size_t)(t0 + r) * K + kk] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * kScanThreads;
+                if (e < n_el) {
+                    const int r = e / per_row, n = 2 * (e % per_row);
+                    *reinterpret_cast<uint32_t *>(smem + (n >> 6) * kAtomBytes + ptx::sw128_offset(r, n & 63)) =
+                        pack2<BF16>(z[u].x, z[u].y);
+                }
+            }
+        }
     }
     ptx::fence_proxy_async_smem();
     ptx::tc_fence_before();
@@ -473,7 +489,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         int cnt = 0;
         for (int j = 0; j < n_jobs; ++j) {
             const int u = j % kRing;
-            const int tile = j % prm.nq, pass = j / prm.nq;
+            const int tile = (j % prm.nq + (int)blockIdx.x) % prm.nq, pass = j / prm.nq;
             if (j == prm.nq) thr = m - win;
             if (*abort_flag) break;
             if (!ptx::mbar_wait(&t2_full[u], (j / kRing) & 1, budget)) {
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 }
                 ptx::mbar_arrive_expect_tx(&b2_full[u], (uint32_t)b2_bytes);
                 uint8_t *B2 = smem + off_b2 + u * b2_bytes;
-                const int tile = j % prm.nq;
+                const int tile = (j % prm.nq + (int)blockIdx.x) % prm.nq;  // CTAs start at different tiles
                 for (int a = 0; a < k2_atoms; ++a)
                     ptx::tma_load_2d(B2 + a * kN2 * 128, &tmap_d, &b2_full[u], a * kAtomElems, tile * kN2);
                 issued = j;
