@@ -52,8 +52,8 @@ typedef enum {
 
 typedef enum {
     SP_PREC_FP32 = 0,  /* FP32 SIMT arithmetic throughout                                    */
-    SP_PREC_FP16 = 1,  /* FP16 tensor-core projections, FP32 accumulate, FP32 top-8 rescoring */
-    SP_PREC_BF16 = 2   /* BF16 tensor-core projections, FP32 accumulate, FP32 top-8 rescoring */
+    SP_PREC_FP16 = 1,  /* FP16 tensor-core projections, FP32 accumulate, FP32 rescoring of a candidate window */
+    SP_PREC_BF16 = 2   /* BF16 tensor-core projections, FP32 accumulate, FP32 rescoring of a candidate window */
 } sp_prec;
 
 typedef struct sp_steering sp_steering;  /* TDOA table + steering matrix W (Eq. 2, 4, 8) */
@@ -158,8 +158,11 @@ int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
  * mode SP_MODE_SRP:            idx = argmax_q Re{W_q X} (needs a materialised W; prec
  *                              must be SP_PREC_FP32).
  * mode SP_MODE_SVD_EXHAUSTIVE: idx = argmax_q Re{D_q Z} (Eq. 14).  With FP16/BF16 the
- *                              scan keeps each frame's 8 best candidates and rescores
- *                              them in FP32 against FP32 Z and D.
+ *                              reduced-precision scan collects, per frame, every class
+ *                              whose score lies within the scan's rounding bound of the
+ *                              frame's maximum (at most 16, else all classes) and
+ *                              rescores them in FP32 against FP32 Z and D, so the result
+ *                              equals an FP32 scan of the same Z.
  * mode SP_MODE_SVD_KDTREE:     idx = nearest D^_q to conj(Z/||Z||) by exact k-d tree
  *                              search (Eq. 15), FP32 distances.
  *
