@@ -138,6 +138,32 @@ int sp_basis_kdtree_info(const sp_basis *b, int *n_nodes, int *leaf_size, int *d
 void sp_basis_destroy(sp_basis *b);
 
 /* ---------------------------------------------------------------------------------
+ * Persistence of the offline phase (Algorithm 1, offline steps 1-3): the array geometry
+ * and grid that define W (Eq. 2, 4), the rank K of Eq. 11, V and D = U S (Eq. 12, 13).
+ *
+ * sp_save_basis writes b to path (a new file, or overwritten): a little-endian binary
+ * with an 80-byte header (magic "SVDPHAT1", version 1, M, Q, N, K, number of singular
+ * values, fs, c, delta), the FP64 arrays mic [M][3], dirs [Q][3], sigma^2, V [L][K] and
+ * D [Q][K] (complex as re, im pairs), and an FNV-1a 64 checksum of all preceding bytes.
+ * Returns SP_EINVAL if the file cannot be opened or written.
+ *
+ * sp_load_basis reads such a file, rebuilds the steering handle (flags as in
+ * sp_build_steering: SP_STEER_MATERIALIZE_W or 0), the device operands and the k-d tree
+ * on the current device, and returns a basis that OWNS its steering handle (released by
+ * sp_basis_destroy; obtain it with sp_basis_steering, never destroy it separately).
+ * Results through a loaded basis are bit-identical to those through the saved one.
+ * A malformed file (wrong magic or version, sizes out of range, a length that does not
+ * match the header, a checksum mismatch, non-finite values) gives SP_EINVAL before any
+ * device work; *out is NULL on every error.  K_out may be NULL.
+ *
+ * sp_basis_steering returns the steering handle a basis was built on (borrowed: valid
+ * while the basis lives).
+ * --------------------------------------------------------------------------------- */
+int sp_save_basis(const sp_basis *b, const char *path);
+int sp_load_basis(const char *path, int flags, sp_basis **out, int *K_out);
+int sp_basis_steering(const sp_basis *b, const sp_steering **out);
+
+/* ---------------------------------------------------------------------------------
  * Online step 1 (Eq. 3, Eq. 7) on its own: PHAT cross spectra of all pairs.
  * frames_dev: device [T][M][B] complex64 (8-byte aligned).  x_dev: device [T][L]
  * complex64, column p*B + k.  T >= 0 (T = 0 is a no-op).

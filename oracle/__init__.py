@@ -261,13 +261,14 @@ def nn_brute(Dhat: np.ndarray, Z: np.ndarray):
     Zh = np.conj(Z / zn[:, None])
     out_i = np.empty(Z.shape[0], dtype=np.int64)
     out_d = np.empty(Z.shape[0])
-    for t0 in range(0, Z.shape[0], 256):
-        zz = Zh[t0:t0 + 256]
+    step = max(1, min(256, (1 << 23) // max(1, Dhat.size)))   # frames per block (memory only)
+    for t0 in range(0, Z.shape[0], step):
+        zz = Zh[t0:t0 + step]
         diff = Dhat[None, :, :] - zz[:, None, :]
         d2 = np.sum(diff.real * diff.real + diff.imag * diff.imag, axis=2)
         i = np.argmin(d2, axis=1)
-        out_i[t0:t0 + 256] = i
-        out_d[t0:t0 + 256] = d2[np.arange(len(i)), i]
+        out_i[t0:t0 + step] = i
+        out_d[t0:t0 + step] = d2[np.arange(len(i)), i]
     return out_i, out_d
 
 

@@ -2,9 +2,9 @@
 the exhaustive Re{D Z} argmax or the k-d tree search, and plain SRP-PHAT beside them, all in
 hand-written CUDA behind the C ABI of ``include/svdphat.h`` (libsvdphat.so)."""
 from .api import (MODE, PREC, Basis, Steering, SvdPhatError, build_steering, check_status, exported_symbols,
-                  lib, localize, localize_host, localize_noalloc, localize_srp, phat, project, set_wait_budget,
-                  svd_reduce)
+                  lib, load_basis, localize, localize_host, localize_noalloc, localize_srp, phat, project,
+                  save_basis, set_wait_budget, svd_reduce)
 
 __all__ = ["MODE", "PREC", "Basis", "Steering", "SvdPhatError", "build_steering", "check_status",
-           "exported_symbols", "lib", "localize", "localize_host", "localize_noalloc", "localize_srp", "phat", "project",
-           "set_wait_budget", "svd_reduce"]
+           "exported_symbols", "lib", "load_basis", "localize", "localize_host", "localize_noalloc", "localize_srp", "phat", "project",
+           "save_basis", "set_wait_budget", "svd_reduce"]

@@ -49,6 +49,9 @@ _SIGS = {
     "sp_basis_d": ([_vp, _dp], ctypes.c_int),
     "sp_basis_kdtree_info": ([_vp, _ip, _ip, _ip], ctypes.c_int),
     "sp_basis_destroy": ([_vp], None),
+    "sp_save_basis": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "sp_load_basis": ([ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_vp), _ip], ctypes.c_int),
+    "sp_basis_steering": ([_vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "sp_phat": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
     "sp_project": ([_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
     "sp_localize": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -127,11 +130,25 @@ class Steering:
                                    float(fs), float(c), int(N),
                                    STEER_MATERIALIZE_W if materialize_w else 0, ctypes.byref(h)))
         self._h = h
+        self._owned = True
+        self._dims()
+        self.materialized = materialize_w
+
+    @classmethod
+    def _borrowed(cls, h, materialized: bool):
+        """A view of a steering handle owned by a loaded basis (never destroyed here)."""
+        self = cls.__new__(cls)
+        self._h = h
+        self._owned = False
+        self._dims()
+        self.materialized = materialized
+        return self
+
+    def _dims(self):
         v = [ctypes.c_int() for _ in range(5)]
-        _check("sp_steering_dims", L.sp_steering_dims(h, *[ctypes.byref(x) for x in v]))
+        _check("sp_steering_dims", lib().sp_steering_dims(self._h, *[ctypes.byref(x) for x in v]))
         self.M, self.P, self.Q, self.N, self.B = (x.value for x in v)
         self.L = self.P * self.B
-        self.materialized = materialize_w
 
     @property
     def handle(self):
@@ -157,7 +174,7 @@ class Steering:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and h.value and _lib is not None:
+        if getattr(self, "_owned", False) and h is not None and h.value and _lib is not None:
             _lib.sp_steering_destroy(h)
             self._h = None
 
@@ -174,6 +191,26 @@ class Basis:
         self.steering = steering
         self.K = K.value
         self.delta = delta
+
+    @classmethod
+    def load(cls, path, materialize_w: bool = False) -> "Basis":
+        """sp_load_basis: a basis saved by ``save``; it owns its steering handle."""
+        h = _vp()
+        K = ctypes.c_int()
+        _check("sp_load_basis", lib().sp_load_basis(os.fsencode(path), STEER_MATERIALIZE_W if materialize_w else 0,
+                                                    ctypes.byref(h), ctypes.byref(K)))
+        self = cls.__new__(cls)
+        self._h = h
+        self.K = K.value
+        sh = _vp()
+        _check("sp_basis_steering", lib().sp_basis_steering(h, ctypes.byref(sh)))
+        self.steering = Steering._borrowed(sh, materialize_w)
+        self.delta = None
+        return self
+
+    def save(self, path):
+        """sp_save_basis: write the offline results (geometry, K, V, D) to ``path``."""
+        _check("sp_save_basis", lib().sp_save_basis(self._h, os.fsencode(path)))
 
     @property
     def handle(self):
@@ -214,6 +251,14 @@ def build_steering(mic_xyz, dirs, fs, c, N, materialize_w=False) -> Steering:
 
 def svd_reduce(steering: Steering, delta: float) -> Basis:
     return Basis(steering, delta)
+
+
+def save_basis(basis: Basis, path) -> None:
+    basis.save(path)
+
+
+def load_basis(path, materialize_w: bool = False) -> Basis:
+    return Basis.load(path, materialize_w)
 
 
 def phat(frames):

@@ -140,6 +140,7 @@ struct sp_basis {
     mutable cudaStream_t copy_stream = nullptr;      // host-path copies
     mutable cudaEvent_t ev_loaded[2] = {nullptr, nullptr};
     mutable cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    sp_steering *owned_st = nullptr;   // set when the basis was loaded from a file
     ~sp_basis() {
         sp::tc_release(this);
         for (int i = 0; i < 2; ++i) {
@@ -147,6 +148,7 @@ struct sp_basis {
             if (ev_free[i]) cudaEventDestroy(ev_free[i]);
         }
         if (copy_stream) cudaStreamDestroy(copy_stream);
+        delete owned_st;
     }
 };
 
@@ -174,6 +176,7 @@ int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *
                   cudaStream_t s);
 int tc_prepare(sp_basis *b);   // upload GEMM1/GEMM2 operands in the tensor-core layouts
 int reduce_basis(const sp_steering *st, double delta, sp_basis *b);
+int install_basis(sp_basis *b);   // device copies of b->V, b->D (host FP64, filled)
 int build_kdtree(sp_basis *b);
 int build_classes(sp_steering *st);   // rep_of / reps from the TDOA table (host)
 }  // namespace sp

@@ -205,6 +205,31 @@ static int rank_rule(const std::vector<double> &s2, double trace, double delta) 
     return K;
 }
 
+// FP32 device copies of the FP64 host basis: V^T [K][L] and D [Q][K] as complex64, and the
+// D rows of the class representatives.
+int install_basis(sp_basis *b) {
+    const sp_steering *st = b->st;
+    const int K = b->K, L = st->L, Q = st->Q;
+    std::vector<float> vt((size_t)K * L * 2), dc((size_t)Q * K * 2);
+    for (int l = 0; l < L; ++l)
+        for (int k = 0; k < K; ++k) {
+            vt[((size_t)k * L + l) * 2] = (float)b->V[((size_t)l * K + k) * 2];
+            vt[((size_t)k * L + l) * 2 + 1] = (float)b->V[((size_t)l * K + k) * 2 + 1];
+        }
+    for (size_t i = 0; i < dc.size(); ++i) dc[i] = (float)b->D[i];
+    const int nr = (int)st->reps.size();
+    std::vector<float> dcr((size_t)nr * K * 2);
+    for (int r = 0; r < nr; ++r)
+        for (int k = 0; k < 2 * K; ++k) dcr[(size_t)r * K * 2 + k] = dc[(size_t)st->reps[r] * K * 2 + k];
+    SP_TRY(b->Dc32r.reserve(dcr.size() * 4));
+    SP_CUDA(cudaMemcpy(b->Dc32r.p, dcr.data(), dcr.size() * 4, cudaMemcpyHostToDevice));
+    SP_TRY(b->Vc32.reserve(vt.size() * 4));
+    SP_TRY(b->Dc32.reserve(dc.size() * 4));
+    SP_CUDA(cudaMemcpy(b->Vc32.p, vt.data(), vt.size() * 4, cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMemcpy(b->Dc32.p, dc.data(), dc.size() * 4, cudaMemcpyHostToDevice));
+    return SP_OK;
+}
+
 int reduce_basis(const sp_steering *st, double delta, sp_basis *b) {
     const int Q = st->Q, L = st->L;
     const int nmin = std::min(Q, L);
@@ -293,27 +318,7 @@ int reduce_basis(const sp_steering *st, double delta, sp_basis *b) {
             b->D[2 * i] = D[i].real();
             b->D[2 * i + 1] = D[i].imag();
         }
-        // FP32 device copies: V^T [K][L] and D [Q][K] as complex64
-        std::vector<float> vt((size_t)K * L * 2), dc((size_t)Q * K * 2);
-        for (int l = 0; l < L; ++l)
-            for (int k = 0; k < K; ++k) {
-                vt[((size_t)k * L + l) * 2] = (float)V[(size_t)l * K + k].real();
-                vt[((size_t)k * L + l) * 2 + 1] = (float)V[(size_t)l * K + k].imag();
-            }
-        for (size_t i = 0; i < D.size(); ++i) {
-            dc[2 * i] = (float)D[i].real();
-            dc[2 * i + 1] = (float)D[i].imag();
-        }
-        const int nr = (int)st->reps.size();
-        std::vector<float> dcr((size_t)nr * K * 2);
-        for (int r = 0; r < nr; ++r)
-            for (int k = 0; k < 2 * K; ++k) dcr[(size_t)r * K * 2 + k] = dc[(size_t)st->reps[r] * K * 2 + k];
-        SP_TRY(b->Dc32r.reserve(dcr.size() * 4));
-        SP_CUDA(cudaMemcpy(b->Dc32r.p, dcr.data(), dcr.size() * 4, cudaMemcpyHostToDevice));
-        SP_TRY(b->Vc32.reserve(vt.size() * 4));
-        SP_TRY(b->Dc32.reserve(dc.size() * 4));
-        SP_CUDA(cudaMemcpy(b->Vc32.p, vt.data(), vt.size() * 4, cudaMemcpyHostToDevice));
-        SP_CUDA(cudaMemcpy(b->Dc32.p, dc.data(), dc.size() * 4, cudaMemcpyHostToDevice));
+        SP_TRY(install_basis(b));
         return SP_OK;
     }
     return fail(SP_ENOTIMPL, "svd_reduce: rank did not settle within the block-size limit");

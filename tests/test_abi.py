@@ -76,3 +76,45 @@ def test_other_entry_points_reject_null_handles(lib):
     assert lib.sp_basis_info(None, None, None, None, 0) == api.SP_EINVAL
     lib.sp_steering_destroy(None)
     lib.sp_basis_destroy(None)
+
+
+def _basis_file(path, M=3, Q=4, N=16, K=2, n_sigma=3, magic=b"SVDPHAT1", version=1, corrupt=0, truncate=0):
+    """A file in the documented basis layout (header, FP64 payload, FNV-1a 64 checksum)."""
+    import struct
+    P, B = M * (M - 1) // 2, N // 2 + 1
+    L = P * B
+    nd = 3 * M + 3 * Q + n_sigma + 2 * L * K + 2 * Q * K
+    hdr = magic + struct.pack("<II6i3dQQ", version, 80, M, Q, N, K, n_sigma, 0, 16000.0, 343.0, 1e-5, nd * 8, 0)
+    body = np.ones(nd).tobytes()
+    h = 1469598103934665603
+    for byte in hdr + body:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    data = bytearray(hdr + body + struct.pack("<Q", h))
+    if corrupt:
+        data[80 + corrupt] ^= 0x40
+    if truncate:
+        data = data[:-truncate]
+    with open(path, "wb") as f:
+        f.write(bytes(data))
+
+
+@pytest.mark.parametrize("kw", [dict(magic=b"SVDPHAT0"), dict(version=2), dict(corrupt=17), dict(truncate=8),
+                                dict(K=0), dict(K=5), dict(n_sigma=1), dict(N=15), dict(M=1)])
+def test_load_basis_rejects_malformed_files(lib, tmp_path, kw):
+    """Every malformed file is refused with SP_EINVAL before any device work."""
+    path = str(tmp_path / "basis.bin")
+    _basis_file(path, **kw)
+    out = ctypes.c_void_p(1)
+    assert lib.sp_load_basis(path.encode(), 0, ctypes.byref(out), None) == api.SP_EINVAL
+    assert out.value is None
+    assert len(lib.sp_last_error()) > 0
+
+
+def test_load_basis_rejects_missing_file_and_null_arguments(lib, tmp_path):
+    out = ctypes.c_void_p()
+    assert lib.sp_load_basis(str(tmp_path / "none.bin").encode(), 0, ctypes.byref(out), None) == api.SP_EINVAL
+    assert lib.sp_load_basis(None, 0, ctypes.byref(out), None) == api.SP_EINVAL
+    assert lib.sp_load_basis(b"x", 0, None, None) == api.SP_EINVAL
+    assert lib.sp_load_basis(b"x", 4, ctypes.byref(out), None) == api.SP_EINVAL
+    assert lib.sp_save_basis(None, b"x") == api.SP_EINVAL
+    assert lib.sp_basis_steering(None, ctypes.byref(out)) == api.SP_EINVAL

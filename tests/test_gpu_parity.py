@@ -43,7 +43,17 @@ def _setup(name, T):
     return d
 
 
-CONFIGS = [("linear_q642", 100), ("planar_q2562", 777)]
+CONFIGS = [("linear_q642", 100), ("planar_q2562", 777), ("array3d_q10242", 256)]
+
+
+def _sqdist(Dhat, Zq):
+    """||Dhat_q - Zq_t||^2 for every (t, q), in blocks of frames (FP64)."""
+    out = np.empty((Zq.shape[0], Dhat.shape[0]))
+    step = max(1, (1 << 23) // Dhat.size)
+    for t0 in range(0, Zq.shape[0], step):
+        diff = Dhat[None, :, :] - Zq[t0:t0 + step, None, :]
+        out[t0:t0 + step] = np.sum(diff.real ** 2 + diff.imag ** 2, axis=2)
+    return out
 
 
 def _agree(d, idx, Y, margin_tol=1e-4, min_agree=0.995):
@@ -170,7 +180,7 @@ def test_localize_kdtree(name, T, prec):
     Dhat = D / np.linalg.norm(D, axis=1, keepdims=True)
     nn, d2 = O.nn_brute(Dhat, Zg)
     Zh = np.conj(Zg / np.linalg.norm(Zg, axis=1, keepdims=True))
-    dist = np.sum(np.abs(Dhat[None, :, :] - Zh[:, None, :]) ** 2, axis=2)
+    dist = _sqdist(Dhat, Zh)
     cls = d["cls"]
     dsec = np.where(cls[None, :] == cls[nn][:, None], np.inf, dist).min(axis=1)
     clear = dsec - d2 > 1e-5
@@ -180,7 +190,7 @@ def test_localize_kdtree(name, T, prec):
     Dh = d["ob"]["Dhat"]
     ref, rd2 = O.nn_brute(Dh, d["Z"])
     Zo = np.conj(d["Z"] / np.linalg.norm(d["Z"], axis=1, keepdims=True))
-    od = np.sum(np.abs(Dh[None, :, :] - Zo[:, None, :]) ** 2, axis=2)
+    od = _sqdist(Dh, Zo)
     osec = np.where(cls[None, :] == cls[ref][:, None], np.inf, od).min(axis=1)
     big = (osec - rd2) > 1e-4
     assert np.all(cls[idx[big]] == cls[ref[big]])
@@ -271,3 +281,24 @@ def test_bench_workload_full_size_sampled():
         _agree(d, idx, Y)
         sref = O.score_row(tau, idx, X, wl["N"])
         assert np.max(np.abs(score.cpu().numpy()[sel] - sref)) <= 2e-5 * W.shape[1]
+
+
+def test_save_load_basis_roundtrip(tmp_path):
+    """A basis written by sp_save_basis and read back by sp_load_basis (with its own steering
+    handle) gives bit-identical results on every search mode."""
+    d = _setup("planar_q2562", 777)
+    path = str(tmp_path / "planar.svdphat")
+    d["b"].save(path)
+    b2 = sp.load_basis(path)
+    assert b2.K == d["b"].K
+    assert np.array_equal(b2.V(), d["b"].V()) and np.array_equal(b2.D(), d["b"].D())
+    assert np.array_equal(b2.steering.tau(), d["st"].tau())
+    assert np.array_equal(b2.steering.classes(), d["st"].classes())
+    for mode, prec in [("svd_exhaustive", "fp16"), ("svd_exhaustive", "bf16"), ("svd_exhaustive", "fp32"),
+                       ("svd_kdtree", "fp16")]:
+        r1 = sp.localize(d["b"], d["frames"], mode, prec)
+        r2 = sp.localize(b2, d["frames"], mode, prec)
+        for a, b in zip(r1, r2):
+            assert torch.equal(a, b)
+    sp.check_status()
+    del b2
