@@ -162,6 +162,126 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+C4_UNIQUE, C4_REPEAT = 32768, 32
+LEARNED_N_TOP, LEARNED_THETA = 8, 0.2
+
+
+def bench_array3d(sp, I, torch):
+    """The k-d tree and learned-proposal forms on the 3-D 7-mic array, Q = 10242 (level-5
+    grid), K = 71: 1,048,576 frames per pass (32,768 unique frames of 1-2 white sources in
+    isotropic noise at 0-20 dB, repeated 32 times on the device).  The proposal (level-3
+    cells, 2K -> 256 -> 256 -> 642) is trained first, untimed, on 65,536 frames of 1-3
+    sources the method labels itself."""
+    wl = I.workload("array3d_q10242", T=C4_UNIQUE, seed_offset=11)
+    st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"])
+    b = sp.svd_reduce(st, wl["delta"])
+    uniq = torch.from_numpy(wl["frames"]).cuda()
+    frames = uniq.repeat(C4_REPEAT, 1, 1)
+    T = frames.shape[0]
+    rng = np.random.default_rng(I.SEED_BASE + 50)
+    tr, _, _ = I.training_frames(rng, wl["mic_xyz"], 65536, wl["N"], wl["fs"], wl["c"])
+    p = sp.Proposal(b, I.icosphere(3), seed=5)
+    x, y = p.examples(torch.from_numpy(tr).cuda(), "fp16")
+    t0 = time.perf_counter()
+    losses = p.train(x, y, epochs=6, batch=512, lr=1e-3, seed=6)
+    train_s = time.perf_counter() - t0
+    del x, y, tr
+
+    def rate(fn, n):
+        return _rate(fn, n, T, torch)
+
+    ex = sp.localize(b, uniq, "svd_exhaustive", "fp16", score=False)[0]
+    li, _, _, fb = p.localize(uniq, "fp16", n_top=LEARNED_N_TOP, theta=LEARNED_THETA, score=False)
+    kd = sp.localize(b, uniq, "svd_kdtree", "fp16", score=False)[0]
+    torch.cuda.synchronize()
+    # per-stage times (ms per pass of T frames)
+    Z = sp.project(b, frames, "fp16")
+    zn2 = (Z.real ** 2 + Z.imag ** 2).sum(dim=1).float()
+    ms = lambda fn, n: T / rate(fn, n) * 1000
+    t_proj = ms(lambda: sp.project(b, frames, "fp16"), 3)
+    t_mlp = ms(lambda: p.infer(Z, zn2), 3)
+    t_exh = ms(lambda: sp.localize(b, frames, "svd_exhaustive", "fp16"), 3)
+    t_exh_ns = ms(lambda: sp.localize(b, frames, "svd_exhaustive", "fp16", score=False), 3)
+    t_lrn = ms(lambda: p.localize(frames, "fp16", n_top=LEARNED_N_TOP, theta=LEARNED_THETA, fallback=False), 3)
+    t_lrn_ns = ms(lambda: p.localize(frames, "fp16", n_top=LEARNED_N_TOP, theta=LEARNED_THETA, score=False,
+                                     fallback=False), 3)
+    t_kd = ms(lambda: sp.localize(b, frames, "svd_kdtree", "fp16"), 1)
+    del Z, zn2
+    out = {
+        "workload": f"array3d_q10242: 7-mic 3-D array, Q=10242, N=512, K={b.K}, {T} frames per pass "
+                    f"({C4_UNIQUE} unique x {C4_REPEAT}), 1-2 sources, isotropic noise 0-20 dB",
+        "svd_exhaustive_fp16_frames_per_s": T / t_exh * 1000,
+        "svd_learned_fp16_frames_per_s": T / t_lrn * 1000,
+        "svd_kdtree_fp16_frames_per_s": T / t_kd * 1000,
+        "ms_per_pass": {"svd_proj_kernel": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
+                        "mlp_tc_kernel": t_mlp, "rescore_and_fallback_scan": t_lrn_ns - t_proj - t_mlp,
+                        "score_row_kernel": t_exh - t_exh_ns, "kdtree": t_kd - (t_exh - t_exh_ns) - t_proj},
+        "learned": {"n_top": LEARNED_N_TOP, "theta": LEARNED_THETA, "cells": 642, "hidden": [256, 256],
+                    "train_frames": 65536, "epochs": 6, "train_s": train_s,
+                    "final_loss": float(losses[-1]),
+                    "fallback_fraction": float(fb.float().mean()),
+                    "agreement_vs_exhaustive": float((li == ex).float().mean())},
+        "kdtree_agreement_vs_exhaustive": float((kd == ex).float().mean()),
+    }
+    return out
+
+
+N_STREAMS, N_CONFIGS = 256, 16
+
+
+def bench_batched(sp, I, torch):
+    """The batched form: 256 streams in one CUDA-graph launch (autotuned).  Stream s uses one
+    of 16 seeded configurations (array of 4-12 mics in a 5 cm-radius ball, Q in {642, 2562},
+    N in {256, 512}; bases built once per configuration) and its own 50-2000 frames (a
+    seeded slice of that configuration's 2000 frames).  Reported beside the same streams
+    localised one sp_localize call after another."""
+    cfgs = I.batched_streams(N_CONFIGS, M_range=(4, 12), Q_choices=(642, 2562), N_choices=(256, 512),
+                             T_range=(2000, 2000), seed_offset=100)
+    bases, pools = [], []
+    t0 = time.perf_counter()
+    for wl in cfgs:
+        st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"])
+        bases.append(sp.svd_reduce(st, wl["delta"]))
+        pools.append(torch.from_numpy(wl["frames"]).cuda())
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(I.SEED_BASE + 2)
+    sb, sf = [], []
+    for s_ in range(N_STREAMS):
+        c = int(rng.integers(0, N_CONFIGS))
+        T = int(rng.integers(50, 2001))
+        o = int(rng.integers(0, 2000 - T + 1))
+        sb.append(bases[c])
+        sf.append(pools[c][o:o + T].contiguous())
+    total = sum(f.shape[0] for f in sf)
+    t0 = time.perf_counter()
+    bt = sp.Batch(sb, sf, "svd_exhaustive", "fp16", autotune=True)
+    tune_s = time.perf_counter() - t0
+    g_rate = _rate(bt.run, 10, total, torch)
+
+    def serial():   # FP32 where a basis has no tensor-core plan, as in the graph
+        for b, f in zip(sb, sf):
+            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 144 else "fp16")
+    s_rate = _rate(serial, 3, total, torch)
+    ks = sorted({b.K for b in bases})
+    return {"workload": f"{N_STREAMS} streams, {total} frames, {N_CONFIGS} configurations (M 4-12, Q 642/2562, "
+                        f"N 256/512, K {ks[0]}-{ks[-1]}), 50-2000 frames per stream",
+            "graph_frames_per_s": g_rate, "serial_frames_per_s": s_rate, "plan": bt.info(),
+            "basis_setup_s": setup_s, "autotune_s": tune_s}
+
+
+def _rate(fn, n, T, torch):
+    fn()
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    a.record(stream)
+    for _ in range(n):
+        fn()
+    z.record(stream)
+    torch.cuda.synchronize()
+    return T * n / (a.elapsed_time(z) / 1000)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +387,16 @@ def main():
         sp.localize_host(b, frames_host, "svd_exhaustive", args.prec, out=hout)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    # the host link alone: one plain pinned host -> device copy of the same frames
+    dst = torch.empty_like(frames)
+    dst.copy_(frames_host, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        dst.copy_(frames_host, non_blocking=True)
+    barrier()
+    h2d_gbs = 3 * frames_host.numel() * 8 / (time.perf_counter() - t0) / 1e9
+    del dst
 
     # max over ranks
     if ws > 1:
@@ -297,6 +427,8 @@ def main():
             other = "bf16" if args.prec == "fp16" else "fp16"
             extras[f"svd_{other}_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", other), 5)
             extras["svd_kdtree_fp16_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_kdtree", "fp16"), 3)
+            extras["array3d_q10242"] = bench_array3d(sp, I, torch)
+            extras["batched_256_streams"] = bench_batched(sp, I, torch)
 
         peak, peak_kind = _peaks()
         frame_bytes = st.M * st.B * 8                       # the STFT of one frame
@@ -324,7 +456,7 @@ def main():
                              "sample": "2048 frames of the same workload (PHAT, Z = V^H X, Re{D Z} argmax, "
                                        "online step 4 in FP64 numpy)"},
             "e2e": {"value": T * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T * frame_bytes,
-                    "d2h_bytes_per_step": T * 12},
+                    "d2h_bytes_per_step": T * 12, "host_to_device_copy_GBps": h2d_gbs},
             "clocks": clk,
         }
         line.update(extras)

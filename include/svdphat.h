@@ -58,6 +58,8 @@ typedef enum {
 
 typedef struct sp_steering sp_steering;  /* TDOA table + steering matrix W (Eq. 2, 4, 8) */
 typedef struct sp_basis sp_basis;        /* rank-K basis V, D = U S, D^, k-d tree (Eq. 10-15) */
+typedef struct sp_proposal sp_proposal;  /* learned cell proposal over a basis (no counterpart in the paper) */
+typedef struct sp_batch sp_batch;        /* many streams in one CUDA-graph launch (no counterpart in the paper) */
 
 /* Thread-local message describing the last failure of this thread (never NULL). */
 const char *sp_last_error(void);
@@ -250,6 +252,109 @@ int sp_check_status(void *stream);
 /* For tests: set the iteration budget of every bounded device wait (0 = default).
  * A budget of 1 makes waits give up at once, which exercises SP_ETIMEOUT. */
 int sp_set_wait_budget(long long iterations);
+
+/* =================================================================================
+ * Batched localisation (no counterpart in the paper, whose Algorithm 1 handles one stream
+ * of frames): n independent streams, each with its own basis (array, grid, N, K), frames
+ * and frame count, localised by one CUDA-graph launch whose branches run concurrently.
+ * Each stream computes exactly what sp_localize computes for it (same kernels, same
+ * results); where a basis has no tensor-core path (2K > 144 or M > 16) an FP16/BF16 request
+ * runs that stream in FP32.
+ *
+ * sp_batch_create: bases[i] (must outlive the plan), frames_dev[i] (device [T[i]][M][B]
+ * complex64, the caller's buffer, read at every run), T[i] >= 1, mode and prec as in
+ * sp_localize, idx_dev[i] / score_dev[i] / proj_dev[i] as in sp_localize (score_dev and
+ * proj_dev may be NULL arrays or hold NULL entries).  Shapes and pointers are fixed for the
+ * plan's lifetime.  Synchronous: it runs every stream once (sizing the workspaces), then
+ * captures the graph; with SP_BATCH_AUTOTUNE it builds and times the candidate launch
+ * shapes (branches in {8, 32, 128, n} x tiles per GEMM1 CTA in {1, 2, 4}) and keeps the
+ * fastest.  Errors: SP_EINVAL (bad arguments, per stream as sp_localize), SP_ECUDA.
+ * sp_batch_run: one graph launch on stream (asynchronous).
+ * sp_batch_info: the chosen shape, the measured milliseconds of one launch (autotuned
+ * plans, else 0) and how many streams run in FP32.
+ * sp_localize_batched: create (no autotuning), run once, synchronise, destroy.
+ * ================================================================================= */
+#define SP_BATCH_AUTOTUNE 1
+int sp_batch_create(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
+                    sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
+                    float *const *proj_dev, int flags, void *stream, sp_batch **out);
+int sp_batch_run(sp_batch *bt, void *stream);
+int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, float *ms, int *n_fp32);
+void sp_batch_destroy(sp_batch *bt);
+int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
+                        sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
+                        float *const *proj_dev, void *stream);
+
+/* =================================================================================
+ * Learned direction proposal (no counterpart in the paper).  The paper searches Eq. 14
+ * exhaustively or by the k-d tree of Eq. 15 (Section 3).  This search lets a small
+ * network propose coarse cells of the direction grid and evaluates Eq. 14 only over the
+ * directions of those cells, in FP32; frames the network is unsure of take the exhaustive
+ * scan.  Definitions:
+ *   cell of direction q: the cell direction with the largest dot product with q (after
+ *     normalising both); dot products within 1e-12 of the largest tie, lowest cell wins.
+ *   features of a frame: x = [Re Z_0, Im Z_0, Re Z_1, Im Z_1, ...] / ||Z||, F = 2K reals
+ *     (Z of Eq. 12; x = 0 when ||Z|| = 0).
+ *   network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), logits = W3 h2 + b3.
+ *   parameters (FP32, flat, in this order): W1 [H1][F], b1 [H1], W2 [H2][H1], b2 [H2],
+ *     W3 [C][H2], b3 [C], all row-major.
+ *   loss: mean over the batch of -log softmax(logits)[label]; a label outside [0, C)
+ *     contributes nothing.  Training label: the cell of the frame's Eq. 14 argmax.
+ *   optimiser: Adam (Kingma & Ba, 2015) with beta1 0.9, beta2 0.999, eps 1e-8.
+ * All device pointers are caller-owned; calls are asynchronous on `stream` unless noted.
+ * ================================================================================= */
+
+/* Create a proposal for basis b (which must outlive it): C cell directions cell_dirs
+ * [C][3] (host, need not be unit length), hidden sizes H1, H2 (multiples of 64 in
+ * [64, 256]), 1 <= C <= 4096, 2K <= 256.  Weights are drawn uniformly in
+ * +-sqrt(6 / fan_in) from a counter-based generator keyed by seed; biases are 0.
+ * Synchronous.  Errors: SP_EINVAL (bad arguments), SP_ENOTIMPL (2K > 256). */
+int sp_proposal_create(const sp_basis *b, const double *cell_dirs, int C, int H1, int H2,
+                       unsigned long long seed, sp_proposal **out);
+void sp_proposal_destroy(sp_proposal *p);
+int sp_proposal_dims(const sp_proposal *p, int *F, int *H1, int *H2, int *C, long long *n_params);
+/* cell_of_host: int32 [Q], the cell of every grid direction. */
+int sp_proposal_cells(const sp_proposal *p, int32_t *cell_of_host);
+/* Copy the FP32 parameters to / from host memory (n_params floats).  Synchronous;
+ * setting also resets the Adam state.  Non-finite values give SP_EINVAL. */
+int sp_proposal_get_params(const sp_proposal *p, float *host);
+int sp_proposal_set_params(sp_proposal *p, const float *host);
+
+/* Training examples from T frames (device [T][M][B] complex64): x_dev float [T][F], the
+ * features of Z (FP16/BF16 tensor-core or FP32 projection per prec), and label_dev int32
+ * [T], the cell of the exhaustive Eq. 14 argmax (-1 for a frame without one). */
+int sp_proposal_examples(const sp_proposal *p, const void *frames_dev, int T, sp_prec prec,
+                         float *x_dev, int32_t *label_dev, void *stream);
+
+/* FP32 forward pass of n feature rows x_dev [n][F] -> logits_dev float [n][C]. */
+int sp_proposal_forward_f32(const sp_proposal *p, const float *x_dev, int n, float *logits_dev,
+                            void *stream);
+/* Loss (loss_dev: one float, or NULL) and its gradient grad_dev (float [n_params], the
+ * parameter layout) over n rows, FP32.  Does not change the parameters. */
+int sp_proposal_grad(const sp_proposal *p, const float *x_dev, const int32_t *label_dev, int n,
+                     float *grad_dev, float *loss_dev, void *stream);
+/* One Adam step on the batch: rows x_dev[rows_dev[i]] (rows_dev int32 [n]) or, with
+ * rows_dev NULL, the first n rows.  lr > 0.  loss_dev as above (before the step). */
+int sp_proposal_train_step(sp_proposal *p, const float *x_dev, const int32_t *label_dev,
+                           const int32_t *rows_dev, int n, float lr, float *loss_dev, void *stream);
+
+/* Tensor-core inference of the network (BF16 weights and activations, FP32 accumulate)
+ * from Z (device [T][K] complex64) and ||Z||^2 (device float [T]): top_dev int32 [T][8],
+ * the 8 cells with the largest logits (largest first, ties -> lowest cell), conf_dev float
+ * [T], the largest softmax probability, and logits_dev float [T][C] or NULL. */
+int sp_proposal_infer(const sp_proposal *p, const void *z_dev, const float *zn2_dev, int T,
+                      float *logits_dev, int32_t *top_dev, float *conf_dev, void *stream);
+
+/* The learned search (Algorithm 1 online steps 1-4 with the proposal in step 3): PHAT and
+ * Z = V^H X on the tensor cores (prec SP_PREC_FP16 or SP_PREC_BF16), the network, then
+ * argmax Re{D_q Z} in FP32 over the directions of the n_top (1..8) proposed cells; a frame
+ * whose largest softmax probability is not >= theta takes the exhaustive scan of
+ * sp_localize (SP_MODE_SVD_EXHAUSTIVE).  idx_dev, score_dev, proj_score_dev as in
+ * sp_localize (idx is the lowest index of the winning direction class); fallback_dev
+ * int32 [T] or NULL receives 1 for frames that fell back, else 0. */
+int sp_localize_learned(const sp_proposal *p, const void *frames_dev, int T, sp_prec prec,
+                        int n_top, float theta, int32_t *idx_dev, float *score_dev,
+                        float *proj_score_dev, int32_t *fallback_dev, void *stream);
 
 #ifdef __cplusplus
 }

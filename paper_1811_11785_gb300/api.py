@@ -60,6 +60,27 @@ _SIGS = {
                           _vp], ctypes.c_int),
     "sp_localize_noalloc": ([_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
     "sp_check_status": ([_vp], ctypes.c_int),
+    "sp_proposal_create": ([_vp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                            ctypes.POINTER(_vp)], ctypes.c_int),
+    "sp_proposal_destroy": ([_vp], None),
+    "sp_proposal_dims": ([_vp, _ip, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "sp_proposal_cells": ([_vp, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "sp_proposal_get_params": ([_vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "sp_proposal_set_params": ([_vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "sp_proposal_examples": ([_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "sp_proposal_forward_f32": ([_vp, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "sp_proposal_grad": ([_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "sp_proposal_train_step": ([_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp, _vp], ctypes.c_int),
+    "sp_proposal_infer": ([_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "sp_batch_create": ([ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
+                         ctypes.POINTER(_vp)], ctypes.c_int),
+    "sp_batch_run": ([_vp, _vp], ctypes.c_int),
+    "sp_batch_info": ([_vp, _ip, _ip, ctypes.POINTER(ctypes.c_float), _ip], ctypes.c_int),
+    "sp_batch_destroy": ([_vp], None),
+    "sp_localize_batched": ([ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
+                            ctypes.c_int),
+    "sp_localize_learned": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp, _vp, _vp, _vp,
+                             _vp], ctypes.c_int),
     "sp_set_wait_budget": ([ctypes.c_longlong], ctypes.c_int),
 }
 
@@ -352,3 +373,185 @@ def check_status():
 
 def set_wait_budget(cycles: int):
     _check("sp_set_wait_budget", lib().sp_set_wait_budget(int(cycles)))
+
+
+class Proposal:
+    """Learned cell proposal over a basis (``sp_proposal_*``); keeps its Basis alive."""
+
+    def __init__(self, basis: Basis, cell_dirs, hidden=(256, 256), seed: int = 0):
+        d = np.ascontiguousarray(cell_dirs, dtype=np.float64)
+        h = _vp()
+        _check("sp_proposal_create", lib().sp_proposal_create(basis.handle, d.ctypes.data_as(_dp), d.shape[0],
+                                                              int(hidden[0]), int(hidden[1]), int(seed) & (2**64 - 1),
+                                                              ctypes.byref(h)))
+        self._h = h
+        self.basis = basis
+        v = [ctypes.c_int() for _ in range(4)]
+        n = ctypes.c_longlong()
+        _check("sp_proposal_dims", lib().sp_proposal_dims(h, *[ctypes.byref(x) for x in v], ctypes.byref(n)))
+        self.F, self.H1, self.H2, self.C = (x.value for x in v)
+        self.n_params = n.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def cells(self) -> np.ndarray:
+        out = np.empty(self.basis.steering.Q, dtype=np.int32)
+        _check("sp_proposal_cells", lib().sp_proposal_cells(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check("sp_proposal_get_params", lib().sp_proposal_get_params(
+            self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_params(self, theta) -> None:
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {t.size}")
+        _check("sp_proposal_set_params", lib().sp_proposal_set_params(
+            self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def examples(self, frames, prec="fp16"):
+        """Training features [T][F] (float32) and labels [T] (int32) of device frames."""
+        import torch
+        _frames(frames, self.basis.steering)
+        T = frames.shape[0]
+        x = torch.empty((T, self.F), dtype=torch.float32, device=frames.device)
+        y = torch.empty(T, dtype=torch.int32, device=frames.device)
+        _check("sp_proposal_examples", lib().sp_proposal_examples(self._h, _ptr(frames), T, _prec(prec), _ptr(x),
+                                                                  _ptr(y), _stream()))
+        return x, y
+
+    def forward_f32(self, x):
+        import torch
+        x = x.contiguous()
+        out = torch.empty((x.shape[0], self.C), dtype=torch.float32, device=x.device)
+        _check("sp_proposal_forward_f32", lib().sp_proposal_forward_f32(self._h, _ptr(x), x.shape[0], _ptr(out),
+                                                                        _stream()))
+        return out
+
+    def grad(self, x, labels):
+        """(gradient [n_params], mean loss) of the batch, FP32 on the device."""
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check("sp_proposal_grad", lib().sp_proposal_grad(self._h, _ptr(x.contiguous()), _ptr(labels.contiguous()),
+                                                          x.shape[0], _ptr(g), _ptr(loss), _stream()))
+        return g, loss
+
+    def train_step(self, x, labels, rows=None, lr=1e-3, loss=None):
+        n = x.shape[0] if rows is None else rows.shape[0]
+        _check("sp_proposal_train_step", lib().sp_proposal_train_step(self._h, _ptr(x), _ptr(labels), _ptr(rows), n,
+                                                                      float(lr), _ptr(loss), _stream()))
+
+    def train(self, x, labels, epochs=10, batch=512, lr=1e-3, seed=0):
+        """Adam over shuffled mini-batches of (x, labels); returns the mean loss per epoch."""
+        import torch
+        T = x.shape[0]
+        rng = np.random.default_rng(seed)
+        losses = torch.empty((epochs, (T + batch - 1) // batch), dtype=torch.float32, device=x.device)
+        for e in range(epochs):
+            perm = torch.from_numpy(rng.permutation(T).astype(np.int32)).to(x.device)
+            for i, b0 in enumerate(range(0, T, batch)):
+                rows = perm[b0:b0 + batch]
+                self.train_step(x, labels, rows=rows, lr=lr, loss=losses[e, i:i + 1])
+        return losses.mean(dim=1).cpu().numpy()
+
+    def infer(self, Z, zn2, logits=False):
+        """Tensor-core inference from Z [T][K] complex64 and ||Z||^2 [T]: (top8, conf, logits|None)."""
+        import torch
+        T = Z.shape[0]
+        top = torch.empty((T, 8), dtype=torch.int32, device=Z.device)
+        conf = torch.empty(T, dtype=torch.float32, device=Z.device)
+        lg = torch.empty((T, self.C), dtype=torch.float32, device=Z.device) if logits else None
+        _check("sp_proposal_infer", lib().sp_proposal_infer(self._h, _ptr(Z.contiguous()), _ptr(zn2.contiguous()), T,
+                                                            _ptr(lg), _ptr(top), _ptr(conf), _stream()))
+        return top, conf, lg
+
+    def localize(self, frames, prec="fp16", n_top=4, theta=0.5, score=True, proj=True, fallback=True):
+        """sp_localize_learned: returns (idx, score|None, proj|None, fallback|None)."""
+        import torch
+        _frames(frames, self.basis.steering)
+        T = frames.shape[0]
+        idx = torch.empty(T, dtype=torch.int32, device=frames.device)
+        sc = torch.empty(T, dtype=torch.float32, device=frames.device) if score else None
+        pj = torch.empty(T, dtype=torch.float32, device=frames.device) if proj else None
+        fb = torch.empty(T, dtype=torch.int32, device=frames.device) if fallback else None
+        _check("sp_localize_learned", lib().sp_localize_learned(self._h, _ptr(frames), T, _prec(prec), int(n_top),
+                                                                float(theta), _ptr(idx), _ptr(sc), _ptr(pj), _ptr(fb),
+                                                                _stream()))
+        return idx, sc, pj, fb
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sp_proposal_destroy(h)
+            self._h = None
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))(*[None if t is None else t.data_ptr() for t in items])
+    return arr
+
+
+class Batch:
+    """A batch plan (``sp_batch_*``): many streams, one CUDA-graph launch per ``run()``.
+
+    ``frames`` is a list of CUDA complex64 tensors [T_i][M_i][B_i] (kept alive and read at
+    every run); results land in ``self.idx`` / ``self.score`` / ``self.proj`` (lists of
+    tensors, one per stream)."""
+
+    def __init__(self, bases, frames, mode="svd_exhaustive", prec="fp16", score=True, proj=True, autotune=False):
+        import torch
+        n = len(bases)
+        if len(frames) != n:
+            raise ValueError("one frame tensor per basis")
+        for b, f in zip(bases, frames):
+            _frames(f, b.steering)
+        self.bases, self.frames = list(bases), list(frames)
+        T = [int(f.shape[0]) for f in frames]
+        self.idx = [torch.empty(t, dtype=torch.int32, device=f.device) for t, f in zip(T, frames)]
+        self.score = [torch.empty(t, dtype=torch.float32, device=f.device) for t, f in zip(T, frames)] if score else None
+        self.proj = [torch.empty(t, dtype=torch.float32, device=f.device) for t, f in zip(T, frames)] if proj else None
+        bh = (ctypes.c_void_p * n)(*[b.handle.value for b in bases])
+        Ta = (ctypes.c_int * n)(*T)
+        h = _vp()
+        _check("sp_batch_create", lib().sp_batch_create(
+            n, bh, _ptr_array(frames), Ta, _mode(mode), _prec(prec), _ptr_array(self.idx),
+            _ptr_array(self.score) if score else None, _ptr_array(self.proj) if proj else None,
+            1 if autotune else 0, _stream(), ctypes.byref(h)))
+        self._h = h
+
+    def run(self):
+        _check("sp_batch_run", lib().sp_batch_run(self._h, _stream()))
+
+    def info(self) -> dict:
+        br, tpc, nf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_float()
+        _check("sp_batch_info", lib().sp_batch_info(self._h, ctypes.byref(br), ctypes.byref(tpc), ctypes.byref(ms),
+                                                    ctypes.byref(nf)))
+        return dict(branches=br.value, tiles_per_cta=tpc.value, ms=ms.value, n_fp32=nf.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sp_batch_destroy(h)
+            self._h = None
+
+
+def localize_batched(bases, frames, mode="svd_exhaustive", prec="fp16"):
+    """sp_localize_batched: returns (idx list, score list, proj list)."""
+    import torch
+    n = len(bases)
+    T = [int(f.shape[0]) for f in frames]
+    idx = [torch.empty(t, dtype=torch.int32, device=f.device) for t, f in zip(T, frames)]
+    sc = [torch.empty(t, dtype=torch.float32, device=f.device) for t, f in zip(T, frames)]
+    pj = [torch.empty(t, dtype=torch.float32, device=f.device) for t, f in zip(T, frames)]
+    bh = (ctypes.c_void_p * n)(*[b.handle.value for b in bases])
+    _check("sp_localize_batched", lib().sp_localize_batched(
+        n, bh, _ptr_array(frames), (ctypes.c_int * n)(*T), _mode(mode), _prec(prec), _ptr_array(idx),
+        _ptr_array(sc), _ptr_array(pj), _stream()))
+    return idx, sc, pj

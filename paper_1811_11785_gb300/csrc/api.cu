@@ -245,41 +245,39 @@ static int srp_path(const sp_steering *st, const void *frames, int T, int32_t *i
     return launch_srp_argmax(st->W.p, st->Q, st->L, work.p, T, keys, idx, best, s);
 }
 
-int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec,
-                int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream) {
-    SP_CHECK(b, SP_EINVAL, "sp_localize: null basis");
+}  // extern "C"
+
+namespace sp {
+
+// The online path of one batch of frames with an explicit workspace (sp_localize uses the
+// basis's own; a batch plan gives every stream its own so that streams run concurrently).
+// max_ctas > 0 caps the CTAs of the tensor-core GEMM1 kernel (tiles per CTA = tiles / cap).
+int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec, int32_t *idx_dev,
+                float *score_dev, float *proj_score_dev, cudaStream_t s, DevBuf &work, int max_ctas) {
     const sp_steering *st = b->st;
-    SP_TRY(check_frames(st, frames_dev, T));
-    if (T == 0) return SP_OK;
-    SP_CHECK(idx_dev && aligned(idx_dev, 4), SP_EINVAL, "sp_localize: idx_dev NULL or misaligned");
-    SP_CHECK(!score_dev || aligned(score_dev, 4), SP_EINVAL, "sp_localize: score_dev misaligned");
-    SP_CHECK(!proj_score_dev || aligned(proj_score_dev, 4), SP_EINVAL,
-             "sp_localize: proj_score_dev misaligned");
-    cudaStream_t s = (cudaStream_t)stream;
     switch (mode) {
         case SP_MODE_SRP: {
             SP_CHECK(prec == SP_PREC_FP32, SP_ENOTIMPL, "SRP runs in FP32 only");
-            SP_TRY(srp_path(st, frames_dev, T, idx_dev, proj_score_dev, b->work, s));
+            SP_TRY(srp_path(st, frames_dev, T, idx_dev, proj_score_dev, work, s));
             break;
         }
         case SP_MODE_SVD_EXHAUSTIVE: {
             if (prec == SP_PREC_FP32) {
                 const size_t xbytes = ((size_t)T * st->L * 8 + 255) / 256 * 256;
                 const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
-                SP_TRY(b->work.reserve(xbytes + zbytes + (size_t)T * 8));
-                char *w = b->work.as<char>();
+                SP_TRY(work.reserve(xbytes + zbytes + (size_t)T * 8));
+                char *w = work.as<char>();
                 SP_TRY(launch_phat(frames_dev, T, st->M, st->B, w, s));
                 SP_TRY(launch_project_f32(b, w, T, w + xbytes, s));
-                SP_TRY(launch_svd_scan_f32(b, w + xbytes, T,
-                                           reinterpret_cast<uint64_t *>(w + xbytes + zbytes),
+                SP_TRY(launch_svd_scan_f32(b, w + xbytes, T, reinterpret_cast<uint64_t *>(w + xbytes + zbytes),
                                            idx_dev, proj_score_dev, s));
             } else {
                 SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "bad precision");
                 const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
-                SP_TRY(b->work.reserve(zbytes + (size_t)T * 4));
-                float *zn2 = reinterpret_cast<float *>(b->work.as<char>() + zbytes);
-                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, b->work.p, zn2, s));
-                SP_TRY(launch_svd_scan(b, b->work.p, zn2, T, (int)prec, idx_dev, proj_score_dev, s));
+                SP_TRY(work.reserve(zbytes + (size_t)T * 4));
+                float *zn2 = reinterpret_cast<float *>(work.as<char>() + zbytes);
+                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, zn2, s, max_ctas));
+                SP_TRY(launch_svd_scan(b, work.p, zn2, T, (int)prec, idx_dev, proj_score_dev, s));
             }
             break;
         }
@@ -287,16 +285,16 @@ int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
             const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
             if (prec == SP_PREC_FP32) {
                 const size_t xbytes = ((size_t)T * st->L * 8 + 255) / 256 * 256;
-                SP_TRY(b->work.reserve(xbytes + zbytes));
-                char *w = b->work.as<char>();
+                SP_TRY(work.reserve(xbytes + zbytes));
+                char *w = work.as<char>();
                 SP_TRY(launch_phat(frames_dev, T, st->M, st->B, w, s));
                 SP_TRY(launch_project_f32(b, w, T, w + xbytes, s));
                 SP_TRY(launch_kdtree(b, w + xbytes, T, idx_dev, proj_score_dev, s));
             } else {
                 SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "bad precision");
-                SP_TRY(b->work.reserve(zbytes));
-                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, b->work.p, nullptr, s));
-                SP_TRY(launch_kdtree(b, b->work.p, T, idx_dev, proj_score_dev, s));
+                SP_TRY(work.reserve(zbytes));
+                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, nullptr, s, max_ctas));
+                SP_TRY(launch_kdtree(b, work.p, T, idx_dev, proj_score_dev, s));
             }
             break;
         }
@@ -305,6 +303,30 @@ int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
     }
     if (score_dev) SP_TRY(launch_score_row(st, frames_dev, T, idx_dev, score_dev, s));
     return SP_OK;
+}
+
+int check_localize_args(const sp_basis *b, const void *frames_dev, int T, const int32_t *idx_dev,
+                        const float *score_dev, const float *proj_score_dev) {
+    SP_CHECK(b, SP_EINVAL, "sp_localize: null basis");
+    SP_TRY(check_frames(b->st, frames_dev, T));
+    if (T == 0) return SP_OK;
+    SP_CHECK(idx_dev && aligned(idx_dev, 4), SP_EINVAL, "sp_localize: idx_dev NULL or misaligned");
+    SP_CHECK(!score_dev || aligned(score_dev, 4), SP_EINVAL, "sp_localize: score_dev misaligned");
+    SP_CHECK(!proj_score_dev || aligned(proj_score_dev, 4), SP_EINVAL,
+             "sp_localize: proj_score_dev misaligned");
+    return SP_OK;
+}
+
+}  // namespace sp
+
+extern "C" {
+
+int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec,
+                int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream) {
+    SP_TRY(check_localize_args(b, frames_dev, T, idx_dev, score_dev, proj_score_dev));
+    if (T == 0) return SP_OK;
+    return localize_ws(b, frames_dev, T, mode, prec, idx_dev, score_dev, proj_score_dev, (cudaStream_t)stream,
+                       b->work, 0);
 }
 
 int sp_localize_srp(const sp_steering *st, const void *frames_dev, int T, int32_t *idx_dev,

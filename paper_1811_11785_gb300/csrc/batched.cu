@@ -1,0 +1,234 @@
+// Batched localisation: many independent streams (each its own array, grid, basis and
+// frame count) in one CUDA-graph launch.  Algorithm 1's online path runs per stream
+// exactly as sp_localize runs it; the plan only schedules the streams' kernels as
+// independent branches of one graph so that the GPU runs them concurrently, gives every
+// stream its own workspace, and picks the launch shape by measurement.
+//
+// Shapes and buffers are static per plan (the graph holds the pointers): the caller fills
+// the frame buffers it passed at creation and launches the plan with sp_batch_run.
+//
+// Autotuner: candidate launch shapes are (number of graph branches the streams are spread
+// over) x (tiles per CTA of the GEMM1 kernel: 1, 2 or 4, i.e. a CTA cap of tiles / d per
+// stream); each candidate graph is built and timed (one warm-up, three timed launches with
+// CUDA events) and the fastest is kept.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+struct sp_batch {
+    int n = 0;
+    sp_mode mode = SP_MODE_SVD_EXHAUSTIVE;
+    std::vector<const sp_basis *> b;
+    std::vector<const void *> frames;
+    std::vector<int> T;
+    std::vector<sp_prec> prec;          // per stream: the requested precision, or FP32 where the
+                                        // tensor-core path does not cover the basis
+    std::vector<int32_t *> idx;
+    std::vector<float *> score, proj;
+    std::vector<std::unique_ptr<sp::DevBuf>> work;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t origin = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int branches = 0, tiles_per_cta = 1;
+    float ms = 0.f;                     // measured time of one launch (autotuned plans)
+    ~sp_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto s : side) cudaStreamDestroy(s);
+        for (auto e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (origin) cudaStreamDestroy(origin);
+    }
+};
+
+namespace sp {
+namespace {
+
+int enqueue_stream(sp_batch *bt, int i, cudaStream_t s, int tiles_per_cta) {
+    const int tiles = (bt->T[i] + 127) / 128;
+    const int cap = std::max(1, (tiles + tiles_per_cta - 1) / tiles_per_cta);
+    return localize_ws(bt->b[i], bt->frames[i], bt->T[i], bt->mode, bt->prec[i], bt->idx[i], bt->score[i],
+                       bt->proj[i], s, *bt->work[i], cap);
+}
+
+// Capture every stream's kernels into one graph: stream i on branch i % branches.
+int build_graph(sp_batch *bt, int branches, int tiles_per_cta, cudaGraphExec_t *out) {
+    *out = nullptr;
+    while ((int)bt->side.size() < branches) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        SP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        bt->side.push_back(s);
+        SP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        bt->join.push_back(e);
+    }
+    cudaGraph_t g = nullptr;
+    SP_CUDA(cudaStreamBeginCapture(bt->origin, cudaStreamCaptureModeRelaxed));
+    int rc = SP_OK;
+    if (cudaEventRecord(bt->fork, bt->origin) != cudaSuccess) rc = fail(SP_ECUDA, "batch: fork record");
+    for (int k = 0; k < branches && rc == SP_OK; ++k)
+        if (cudaStreamWaitEvent(bt->side[k], bt->fork, 0) != cudaSuccess) rc = fail(SP_ECUDA, "batch: fork wait");
+    for (int i = 0; i < bt->n && rc == SP_OK; ++i) rc = enqueue_stream(bt, i, bt->side[i % branches], tiles_per_cta);
+    for (int k = 0; k < branches && rc == SP_OK; ++k) {
+        if (cudaEventRecord(bt->join[k], bt->side[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(bt->origin, bt->join[k], 0) != cudaSuccess)
+            rc = fail(SP_ECUDA, "batch: join");
+    }
+    const cudaError_t e = cudaStreamEndCapture(bt->origin, &g);
+    if (rc != SP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(SP_ECUDA, std::string("batch: capture: ") + cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        *out = nullptr;
+        return fail(SP_ECUDA, std::string("batch: instantiate: ") + cudaGetErrorString(ei));
+    }
+    return SP_OK;
+}
+
+int time_graph(cudaGraphExec_t ex, cudaStream_t s, float *ms) {
+    cudaEvent_t a, z;
+    SP_CUDA(cudaEventCreate(&a));
+    SP_CUDA(cudaEventCreate(&z));
+    int rc = SP_OK;
+    if (cudaGraphLaunch(ex, s) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) rc = fail(SP_ECUDA, "batch: launch");
+    for (int r = 0; r < 3 && rc == SP_OK; ++r)
+        if (cudaGraphLaunch(ex, s) != cudaSuccess) rc = fail(SP_ECUDA, "batch: launch");
+    if (rc == SP_OK && (cudaEventRecord(z, s) != cudaSuccess || cudaEventSynchronize(z) != cudaSuccess))
+        rc = fail(SP_ECUDA, "batch: timing");
+    if (rc == SP_OK) {
+        cudaEventElapsedTime(ms, a, z);
+        *ms /= 3.f;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    return rc;
+}
+
+}  // namespace
+}  // namespace sp
+
+using namespace sp;
+
+extern "C" {
+
+int sp_batch_create(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T, sp_mode mode,
+                    sp_prec prec, int32_t *const *idx_dev, float *const *score_dev, float *const *proj_dev, int flags,
+                    void *stream, sp_batch **out) {
+    SP_CHECK(out, SP_EINVAL, "sp_batch_create: out is NULL");
+    *out = nullptr;
+    SP_CHECK(n >= 1 && n <= 65536, SP_EINVAL, "sp_batch_create: n must be in [1, 65536]");
+    SP_CHECK(bases && frames_dev && T && idx_dev, SP_EINVAL, "sp_batch_create: null array");
+    SP_CHECK((flags & ~SP_BATCH_AUTOTUNE) == 0, SP_EINVAL, "sp_batch_create: bad flags");
+    SP_CHECK(prec == SP_PREC_FP32 || prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL,
+             "sp_batch_create: bad precision");
+    for (int i = 0; i < n; ++i) {
+        SP_TRY(check_localize_args(bases[i], frames_dev[i], T[i], idx_dev[i], score_dev ? score_dev[i] : nullptr,
+                                   proj_dev ? proj_dev[i] : nullptr));
+        SP_CHECK(T[i] >= 1, SP_EINVAL, "sp_batch_create: every stream needs T >= 1");
+    }
+    std::unique_ptr<sp_batch> bt(new (std::nothrow) sp_batch());
+    SP_CHECK(bt, SP_ENOMEM, "sp_batch_create: host allocation failed");
+    bt->n = n;
+    bt->mode = mode;
+    for (int i = 0; i < n; ++i) {
+        bt->b.push_back(bases[i]);
+        bt->frames.push_back(frames_dev[i]);
+        bt->T.push_back(T[i]);
+        const bool tc = bases[i]->tc.n1 > 0 && bases[i]->tc_maps;
+        bt->prec.push_back(prec != SP_PREC_FP32 && !tc ? SP_PREC_FP32 : prec);
+        bt->idx.push_back(idx_dev[i]);
+        bt->score.push_back(score_dev ? score_dev[i] : nullptr);
+        bt->proj.push_back(proj_dev ? proj_dev[i] : nullptr);
+        bt->work.emplace_back(new (std::nothrow) DevBuf());
+        SP_CHECK(bt->work.back(), SP_ENOMEM, "sp_batch_create: host allocation failed");
+    }
+    SP_CUDA(cudaStreamCreateWithFlags(&bt->origin, cudaStreamNonBlocking));
+    SP_CUDA(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+    // one eager pass: sizes every workspace (no allocation happens while capturing) and
+    // sets the kernels' attributes
+    for (int i = 0; i < n; ++i) SP_TRY(enqueue_stream(bt.get(), i, bt->origin, 1));
+    SP_CUDA(cudaStreamSynchronize(bt->origin));
+    std::vector<int> br_cand;
+    for (int k : {8, 32, 128})
+        if (k < n) br_cand.push_back(k);
+    br_cand.push_back(n);
+    if (flags & SP_BATCH_AUTOTUNE) {
+        float best = 0.f;
+        for (int br : br_cand)
+            for (int tpc : {1, 2, 4}) {
+                cudaGraphExec_t ex = nullptr;
+                SP_TRY(build_graph(bt.get(), br, tpc, &ex));
+                float ms = 0.f;
+                const int rc = time_graph(ex, bt->origin, &ms);
+                if (rc != SP_OK) {
+                    cudaGraphExecDestroy(ex);
+                    return rc;
+                }
+                if (!bt->exec || ms < best) {
+                    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+                    bt->exec = ex;
+                    best = ms;
+                    bt->branches = br;
+                    bt->tiles_per_cta = tpc;
+                } else {
+                    cudaGraphExecDestroy(ex);
+                }
+            }
+        bt->ms = best;
+    } else {
+        bt->branches = std::min(n, 32);
+        bt->tiles_per_cta = 1;
+        SP_TRY(build_graph(bt.get(), bt->branches, 1, &bt->exec));
+    }
+    (void)stream;
+    *out = bt.release();
+    return SP_OK;
+}
+
+int sp_batch_run(sp_batch *bt, void *stream) {
+    SP_CHECK(bt && bt->exec, SP_EINVAL, "sp_batch_run: null plan");
+    SP_CUDA(cudaGraphLaunch(bt->exec, (cudaStream_t)stream));
+    return SP_OK;
+}
+
+int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, float *ms, int *n_fp32) {
+    SP_CHECK(bt, SP_EINVAL, "sp_batch_info: null plan");
+    if (branches) *branches = bt->branches;
+    if (tiles_per_cta) *tiles_per_cta = bt->tiles_per_cta;
+    if (ms) *ms = bt->ms;
+    if (n_fp32) {
+        int c = 0;
+        for (auto p : bt->prec) c += p == SP_PREC_FP32;
+        *n_fp32 = c;
+    }
+    return SP_OK;
+}
+
+void sp_batch_destroy(sp_batch *bt) { delete bt; }
+
+int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
+                        sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
+                        float *const *proj_dev, void *stream) {
+    sp_batch *bt = nullptr;
+    SP_TRY(sp_batch_create(n, bases, frames_dev, T, mode, prec, idx_dev, score_dev, proj_dev, 0, stream, &bt));
+    int rc = sp_batch_run(bt, stream);
+    if (rc == SP_OK) {
+        const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) rc = fail(SP_ECUDA, std::string("sp_localize_batched: ") + cudaGetErrorString(e));
+    }
+    sp_batch_destroy(bt);
+    return rc;
+}
+
+}  // extern "C"

@@ -3,6 +3,7 @@
 // through the launch_* functions declared here.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +58,7 @@ struct DevBuf {
 // Set by kernels whose bounded waits gave up (see sp_check_status).
 int read_and_clear_device_status(cudaStream_t s, int *status);
 long long wait_budget();
+int device_status_ptr(int **out);   // the status word's device address (current device)
 
 // ---------------------------------------------------------------- tiling of the
 // tensor-core projection (K-dimension layout of GEMM1, chosen for the GPU; the paper's
@@ -166,17 +168,28 @@ int launch_svd_scan_f32(const sp_basis *b, const void *Z, int T, uint64_t *keys,
                         float *best, cudaStream_t s);
 int launch_score_row(const sp_steering *st, const void *frames, int T, const int32_t *idx,
                      float *score, cudaStream_t s);
+int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const int32_t *idx, float *score,
+                      cudaStream_t s);   // SP_ENOTIMPL where its plan does not apply
 // tensor-core path: Z = V^H X (PHAT fused) into z_out [T][K] complex64, then the Re{D Z} scan
 // (zn2_out [T] receives ||Z||^2 per frame, may be null; the scan needs it)
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
-                    cudaStream_t s);
+                    cudaStream_t s, int max_ctas = 0);
 int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
                     float *proj, cudaStream_t s);
 int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
                   cudaStream_t s);
-int tc_prepare(sp_basis *b);   // upload GEMM1/GEMM2 operands in the tensor-core layouts
+int tc_prepare(sp_basis *b);
+// 2-D tensor map of a row-major [rows][inner] fp16 (bf16 = 0) / bf16 (bf16 = 1) array,
+// 128-byte swizzle, box {box_inner, box_rows}
+int encode_tmap_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint64_t rows, uint32_t box_inner,
+                   uint32_t box_rows);
+int num_sms();   // upload GEMM1/GEMM2 operands in the tensor-core layouts
 int reduce_basis(const sp_steering *st, double delta, sp_basis *b);
 int install_basis(sp_basis *b);   // device copies of b->V, b->D (host FP64, filled)
 int build_kdtree(sp_basis *b);
+int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec, int32_t *idx_dev,
+                float *score_dev, float *proj_score_dev, cudaStream_t s, DevBuf &work, int max_ctas);
+int check_localize_args(const sp_basis *b, const void *frames_dev, int T, const int32_t *idx_dev,
+                        const float *score_dev, const float *proj_score_dev);
 int build_classes(sp_steering *st);   // rep_of / reps from the TDOA table (host)
 }  // namespace sp

@@ -391,6 +391,10 @@ int launch_score_row(const sp_steering *st, const void *frames, int T, const int
                      float *score, cudaStream_t s) {
     if (T == 0) return SP_OK;
     SP_CHECK(st->M <= 16, SP_ENOTIMPL, "online step 4 supports M <= 16");
+    {   // bulk-copy version where it applies (16-byte aligned batch, frame pairs <= 48 KB)
+        const int rc = launch_step4_bulk(st, frames, T, idx, score, s);
+        if (rc != SP_ENOTIMPL) return rc;
+    }
     const long long blocks = ((long long)T + 7) / 8;
     auto kern = st->M == 7 ? score_row_kernel<7, true> : st->M <= 8 ? score_row_kernel<8, false> : score_row_kernel<16, false>;
     kern<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, 1.0 / (double)st->N,

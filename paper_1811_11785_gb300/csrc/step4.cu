@@ -1,0 +1,223 @@
+// Online step 4 of Algorithm 1 (Y_qbar = Re{W_qbar X}) with the STFT streamed by bulk copies.
+//
+// Same arithmetic as score_row_kernel (simt.cu): because tau_{q,i,j} = d_j - d_i with
+// d_m = fs/c r_m . u_q, W_ij X_ij = y_i conj(y_j) with y_m[k] = x^_m[k] exp(-2 pi i k d_m / N),
+// and sum_{i<j} Re{y_i conj(y_j)} = (|sum_m y_m|^2 - sum_m |y_m|^2) / 2 per bin.
+//
+// Layout of the work: frames are taken in pairs (2 M B complex64 = 16 M B bytes, so every
+// pair starts 16-byte aligned when the batch does); one CTA per SM walks its pairs through a
+// ring of 4 shared-memory slots filled by one producer thread with cp.async.bulk, while 16
+// consumer warps compute (4 per slot: frame 0 or 1 of the pair x even or odd 32-bin half).
+// The odd last frame of an odd batch is read from global memory by its warps.  Every wait is
+// bounded; a wait that gives up records status bit 4 and the CTA drains and returns.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.h"
+#include "ptx.cuh"
+
+namespace sp {
+namespace {
+
+constexpr int kSlots = 4;
+constexpr int kConsumerWarps = 16;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;
+constexpr float kZero2 = 1e-30f;
+constexpr long long kDrainCycles = 4000000000LL;
+
+struct Step4Params {
+    const float2 *frames;
+    int T, M, B, n_pairs;
+    unsigned pair_bytes;   // 16 M B
+    double inv_n, g;
+    const double *unit, *mic;
+    const int32_t *idx;
+    float *score;
+    int *status;
+    long long budget;
+};
+
+template <int MMAX, bool EXACT>
+__global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Params prm) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int M = EXACT ? MMAX : prm.M;
+    const int B = prm.B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned slot_bytes = (prm.pair_bytes + 127) / 128 * 128;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSlots * slot_bytes);
+    uint64_t *empty = full + kSlots;
+    float *part = reinterpret_cast<float *>(empty + kSlots);          // [slot][frame]
+    volatile int *dec = reinterpret_cast<volatile int *>(part + 2 * kSlots);   // [slot][frame]
+    volatile int *abort_flag = dec + 2 * kSlots;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 4);
+        }
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const int my_pairs = prm.n_pairs > (int)blockIdx.x ? (prm.n_pairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long budget = prm.budget;
+
+    if (warp == kConsumerWarps) {
+        // ---------------- producer: one bulk copy per pair of frames
+        if (lane == 0) {
+            int issued = -1;
+            for (int i = 0; i < my_pairs; ++i) {
+                const int s = i % kSlots;
+                if (*abort_flag) break;
+                if (!ptx::mbar_wait(&empty[s], ((i / kSlots) & 1) ^ 1, budget)) {
+                    *abort_flag = 1;
+                    atomicOr(prm.status, 4);
+                    break;
+                }
+                const long long pair = (long long)blockIdx.x + (long long)i * gridDim.x;
+                const bool whole = 2 * pair + 1 < prm.T;
+                if (whole) {
+                    ptx::mbar_arrive_expect_tx(&full[s], prm.pair_bytes);
+                    ptx::bulk_load(smem + s * slot_bytes,
+                                   reinterpret_cast<const uint8_t *>(prm.frames) + (size_t)pair * prm.pair_bytes,
+                                   prm.pair_bytes, &full[s]);
+                } else {
+                    ptx::mbar_arrive(&full[s]);   // odd last frame: its warps read global memory
+                }
+                issued = i;
+            }
+            for (int i = issued - kSlots + 1; i <= issued; ++i)
+                if (i >= 0) ptx::mbar_wait(&full[i % kSlots], (i / kSlots) & 1, kDrainCycles);
+        }
+        __syncwarp();
+        return;
+    }
+
+    // ---------------- consumers: warp = (slot, frame h of the pair, bin half g)
+    const int s = warp >> 2, h = (warp >> 1) & 1, gh = warp & 1;
+    const float2 *smem_frame = reinterpret_cast<const float2 *>(smem + s * slot_bytes) + (size_t)h * M * B;
+    const int bar_id = 1 + s * 2 + h;   // the two bin halves of frame h (64 threads)
+    for (int i = s; i < my_pairs; i += kSlots) {
+        // Both warps of a frame leave the loop together: the g = 0 warp reads the abort flag
+        // before the barrier and both act on that one reading after it.
+        const bool ok = ptx::mbar_wait_warp(&full[s], (i / kSlots) & 1, budget);
+        if (!ok && lane == 0) {
+            *abort_flag = 1;
+            atomicOr(prm.status, 4);
+        }
+        if (gh == 0 && lane == 0) dec[s * 2 + h] = *abort_flag;
+        ptx::named_bar_sync(bar_id, 64);
+        if (dec[s * 2 + h]) break;
+        const long long pair = (long long)blockIdx.x + (long long)i * gridDim.x;
+        const long long t = 2 * pair + h;
+        const bool whole = 2 * pair + 1 < prm.T;
+        float acc = 0.f;
+        int q = -1;
+        if (t < prm.T) q = prm.idx[t];
+        if (q >= 0) {
+            const float2 *fr = whole ? smem_frame : prm.frames + (size_t)t * M * B;
+            // lane m: d_m / N (split into two floats) and the 64-bin step phasor
+            float my_hi = 0.f, my_lo = 0.f, my_sc = 1.f, my_ss = 0.f;
+            if (lane < M) {
+                const double d = prm.g * ((prm.mic[3 * lane] * prm.unit[3 * q] + prm.mic[3 * lane + 1] * prm.unit[3 * q + 1]) +
+                                          prm.mic[3 * lane + 2] * prm.unit[3 * q + 2]);
+                const double e = d * prm.inv_n;
+                my_hi = (float)e;
+                my_lo = (float)(e - (double)my_hi);
+                const float p1 = 64.f * my_hi;
+                const float r1 = (p1 - rintf(p1)) + 64.f * my_lo;
+                sincospif(-2.f * r1, &my_ss, &my_sc);
+            }
+            float2 ph[MMAX], stp[MMAX];
+            const int k_first = 32 * gh + lane;
+#pragma unroll
+            for (int m = 0; m < MMAX; ++m) {
+                const float ehi = __shfl_sync(0xffffffffu, my_hi, m);
+                const float elo = __shfl_sync(0xffffffffu, my_lo, m);
+                stp[m] = make_float2(__shfl_sync(0xffffffffu, my_sc, m), __shfl_sync(0xffffffffu, my_ss, m));
+                if (m < M) {
+                    const float kf = (float)k_first;
+                    const float p0 = kf * ehi;
+                    const float r0 = (p0 - rintf(p0)) + fmaf(kf, elo, fmaf(kf, ehi, -p0));
+                    float sn, cs;
+                    sincospif(-2.f * r0, &sn, &cs);
+                    ph[m] = make_float2(cs, sn);
+                }
+            }
+            for (int k = k_first; k < B; k += 64) {
+                float sr = 0.f, si = 0.f, en = 0.f;
+#pragma unroll
+                for (int m = 0; m < MMAX; ++m) {
+                    if (m < M) {
+                        const float2 x = fr[(size_t)m * B + k];
+                        const float mag2 = x.x * x.x + x.y * x.y;
+                        const float2 w = ph[m];
+                        const float r = mag2 >= kZero2 ? rsqrtf(mag2) : 0.f;
+                        const float xr = x.x * r, xi = x.y * r;
+                        const float yr = xr * w.x - xi * w.y, yi = xr * w.y + xi * w.x;
+                        sr += yr;
+                        si += yi;
+                        en += yr * yr + yi * yi;
+                        const float2 st = stp[m];
+                        ph[m] = make_float2(w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x);
+                    }
+                }
+                acc += 0.5f * (sr * sr + si * si - en);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        }
+        // the two bin halves of frame h meet at their named barrier
+        if (gh == 1 && lane == 0) part[s * 2 + h] = acc;
+        ptx::named_bar_sync(bar_id, 64);
+        if (gh == 0 && lane == 0 && t < prm.T)
+            prm.score[t] = q < 0 ? __int_as_float(0x7fc00000) : acc + part[s * 2 + h];
+        ptx::named_bar_sync(bar_id, 64);   // part[] and dec[] are reused by the next pair
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&empty[s]);
+    }
+}
+
+}  // namespace
+
+// Returns SP_ENOTIMPL when the bulk-copy plan does not apply (unaligned batch, M > 16, or a
+// frame pair larger than a quarter of the shared memory); the caller then uses
+// score_row_kernel.
+int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const int32_t *idx, float *score,
+                      cudaStream_t s) {
+    if (T == 0) return SP_OK;
+    const unsigned pair_bytes = 16u * (unsigned)st->M * (unsigned)st->B;
+    if (st->M > 16 || (reinterpret_cast<uintptr_t>(frames) & 15) != 0 || pair_bytes > 48u * 1024u)
+        return SP_ENOTIMPL;
+    Step4Params p;
+    p.frames = static_cast<const float2 *>(frames);
+    p.T = T;
+    p.M = st->M;
+    p.B = st->B;
+    p.n_pairs = (T + 1) / 2;
+    p.pair_bytes = pair_bytes;
+    p.inv_n = 1.0 / (double)st->N;
+    p.g = st->fs / st->c;
+    p.unit = st->d_dirs.as<double>();
+    p.mic = st->d_mic.as<double>();
+    p.idx = idx;
+    p.score = score;
+    SP_TRY(device_status_ptr(&p.status));
+    p.budget = wait_budget();
+    const unsigned slot_bytes = (pair_bytes + 127) / 128 * 128;
+    const int smem = (int)(kSlots * slot_bytes + 2 * kSlots * 8 + 4 * kSlots * 4 + 16 + 128);
+    auto kern = st->M == 7 ? step4_bulk_kernel<7, true>
+                           : st->M <= 8 ? step4_bulk_kernel<8, false> : step4_bulk_kernel<16, false>;
+    const int which = st->M == 7 ? 0 : st->M <= 8 ? 1 : 2;
+    static bool attr[3] = {false, false, false};
+    if (!attr[which]) {
+        SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+        attr[which] = true;
+    }
+    const int grid = std::min(p.n_pairs, num_sms());
+    kern<<<grid, kThreads, smem, s>>>(p);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+}  // namespace sp

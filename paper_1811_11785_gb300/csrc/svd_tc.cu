@@ -51,6 +51,22 @@ constexpr long long kDrainBudget = 4000000000LL;     // draining in-flight async
 static long long h_wait_budget = 2000000000LL;
 long long wait_budget() { return h_wait_budget; }
 
+// Device address of the status word, for kernels of other translation units (looked up
+// once per device).
+int device_status_ptr(int **out) {
+    static int *cache[64] = {};
+    int dev = 0;
+    SP_CUDA(cudaGetDevice(&dev));
+    SP_CHECK(dev >= 0 && dev < 64, SP_ENOTIMPL, "device index out of range");
+    if (!cache[dev]) {
+        void *p = nullptr;
+        SP_CUDA(cudaGetSymbolAddress(&p, g_status));
+        cache[dev] = static_cast<int *>(p);
+    }
+    *out = cache[dev];
+    return SP_OK;
+}
+
 int read_and_clear_device_status(cudaStream_t s, int *status) {
     int v = 0, zero = 0;
     SP_CUDA(cudaStreamSynchronize(s));
@@ -277,9 +293,11 @@ __global__ void __launch_bounds__(kProjThreads, 1)
         };
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) load_next(raw[d]);
-        for (int j = 0; j < n_items; j += DEPTH) {
-            if (!step(raw[0])) break;
-            if (DEPTH > 1 && j + 1 < n_items && !step(raw[DEPTH - 1])) break;
+        bool ok = true;
+        for (int j = 0; j < n_items && ok; j += DEPTH) {
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d)
+                if (ok && j + d < n_items) ok = step(raw[d]);
         }
     } else if (warp < kEpiWarp0 + 4) {
         // -------- epilogue: Z of each finished tile, TMEM -> FP32 global
@@ -287,9 +305,9 @@ __global__ void __launch_bounds__(kProjThreads, 1)
         const int r = q4 * 32 + lane;      // frame row within the tile
         for (int li = 0; li < my_tiles; ++li) {
             const int zb = li & 1;
-            if (*abort_flag) break;
-            if (!ptx::mbar_wait(&zfull[zb], (li >> 1) & 1, budget)) {
-                give_up();
+            if (ptx::warp_flag(abort_flag)) break;
+            if (!ptx::mbar_wait_warp(&zfull[zb], (li >> 1) & 1, budget)) {
+                if (lane == 0) give_up();
                 break;
             }
             ptx::tc_fence_after();
@@ -428,6 +446,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     const long long budget = g_wait_budget;
     const long long t0 = (long long)blockIdx.x * 128;
     const int K = prm.K;
+    const int T = prm.T;
 
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) {
@@ -457,7 +476,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * kScanThreads;
                 const int r = e / per_row, kk = e % per_row;
-                z[u] = (e < n_el && kk < K && t0 + r < prm.T) ? prm.Z[(size_t)(t0 + r) * K + kk] : make_float2(0.f, 0.f);
+                z[u] = (e < n_el && kk < K && t0 + r < T) ? prm.Z[(size_t)(t0 + r) * K + kk] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -484,16 +503,16 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     if (warp < 4) {
         const int r = tid;  // TMEM lane = frame row
         const long long frame = t0 + r;
-        const float win = prm.tol_z * sqrtf(frame < prm.T ? prm.zn2[frame] : 0.f) + prm.tol_abs;
+        const float win = prm.tol_z * sqrtf(frame < T ? prm.zn2[frame] : 0.f) + prm.tol_abs;
         float m = -__int_as_float(0x7f800000), thr = 0.f;
         int cnt = 0;
         for (int j = 0; j < n_jobs; ++j) {
             const int u = j % kRing;
             const int tile = (j % prm.nq + (int)blockIdx.x) % prm.nq, pass = j / prm.nq;
             if (j == prm.nq) thr = m - win;
-            if (*abort_flag) break;
-            if (!ptx::mbar_wait(&t2_full[u], (j / kRing) & 1, budget)) {
-                give_up();
+            if (ptx::warp_flag(abort_flag)) break;
+            if (!ptx::mbar_wait_warp(&t2_full[u], (j / kRing) & 1, budget)) {
+                if (lane == 0) give_up();
                 break;
             }
             ptx::tc_fence_after();
@@ -518,7 +537,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             ptx::tc_fence_before();
             ptx::mbar_arrive(&t2_empty[u]);
         }
-        cnt_s[r] = (frame < prm.T && m == m && thr == thr) ? cnt : 0;
+        cnt_s[r] = (frame < T && m == m && thr == thr) ? cnt : 0;
     } else if (warp == 4) {
         if (lane == 0) {
             int issued = -1;
@@ -578,7 +597,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         for (int r0 = 2 * warp; r0 < 128; r0 += 2 * (kScanThreads / 32)) {
             const int r = r0 + h;
             const long long frame = t0 + r;
-            const bool live = frame < prm.T;
+            const bool live = frame < T;
             const int n = live ? cnt_s[r] : 0;
             const int total = n <= kCap ? n : prm.Qr;   // n > kCap: every class
             const float2 *zr = prm.Z + (size_t)(live ? frame : 0) * K;
@@ -649,8 +668,8 @@ static EncodeTiledFn get_encode() {
     return fn;
 }
 
-static int encode_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint64_t rows,
-                     uint32_t box_inner, uint32_t box_rows) {
+int encode_tmap_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint64_t rows,
+                   uint32_t box_inner, uint32_t box_rows) {
     EncodeTiledFn enc = get_encode();
     SP_CHECK(enc != nullptr, SP_ECUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[2] = {inner, rows};
@@ -726,8 +745,8 @@ int tc_prepare(sp_basis *b) {
         SP_TRY(b->Dtc[prec].reserve(hd.size() * 2));
         SP_CUDA(cudaMemcpy(b->Vtc[prec].p, hv.data(), nv * 2, cudaMemcpyHostToDevice));
         SP_CUDA(cudaMemcpy(b->Dtc[prec].p, hd.data(), hd.size() * 2, cudaMemcpyHostToDevice));
-        int rc = encode_2d(&maps->v[prec], b->Vtc[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.n1);
-        if (rc == SP_OK) rc = encode_2d(&maps->d[prec], b->Dtc[prec].p, prec, dcols, Qr, kAtomElems, kN2);
+        int rc = encode_tmap_2d(&maps->v[prec], b->Vtc[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.n1);
+        if (rc == SP_OK) rc = encode_tmap_2d(&maps->d[prec], b->Dtc[prec].p, prec, dcols, Qr, kAtomElems, kN2);
         if (rc != SP_OK) {
             delete maps;
             return rc;
@@ -742,7 +761,7 @@ void tc_release(sp_basis *b) {
     b->tc_maps = nullptr;
 }
 
-static int num_sms() {
+int num_sms() {
     static int n = 0;
     if (n == 0) {
         int dev = 0;
@@ -754,7 +773,7 @@ static int num_sms() {
 }
 
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
-                    cudaStream_t s) {
+                    cudaStream_t s, int max_ctas) {
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
@@ -790,7 +809,7 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     }
     // at least 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM
     const int smem_launch = std::max(smem, 120 * 1024);
-    const int grid = std::min(p.n_tiles, num_sms());
+    const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
     kern<<<grid, kProjThreads, smem_launch, s>>>(maps->v[bf], p);
     SP_CUDA(cudaGetLastError());
     return SP_OK;

@@ -148,6 +148,22 @@ def _windowed_spectra(rng: np.random.Generator, shape: tuple, N: int, win: np.nd
     return np.fft.rfft(x * win, axis=-1)
 
 
+def isotropic_mixing(mic_xyz: np.ndarray, N: int, fs: float, c: float) -> np.ndarray:
+    """Per bin k, a matrix A_k with A_k A_k^T equal to the spherically isotropic coherence
+    Gamma_ij = sinc(2 f_k d_ij / c) (numpy's normalised sinc), f_k = k fs / N: the
+    symmetric square root from the eigendecomposition (negative rounding eigenvalues
+    clipped to 0).  Shape (B, M, M)."""
+    mic_xyz = np.asarray(mic_xyz, dtype=np.float64)
+    d = np.linalg.norm(mic_xyz[:, None, :] - mic_xyz[None, :, :], axis=2)
+    B = N // 2 + 1
+    out = np.empty((B, mic_xyz.shape[0], mic_xyz.shape[0]))
+    for k in range(B):
+        G = np.sinc(2.0 * (k * fs / N) * d / c)
+        lam, U = np.linalg.eigh(G)
+        out[k] = (U * np.sqrt(np.clip(lam, 0.0, None))) @ U.T
+    return out
+
+
 def plane_wave_frames(
     rng: np.random.Generator,
     mic_xyz: np.ndarray,
@@ -168,8 +184,11 @@ def plane_wave_frames(
     transformed with an N-point real FFT; microphone m receives it advanced by
     ``fs/c * r_m . u`` samples, applied as a phase ramp in frequency
     (a fractional delay).  Noise is independent white noise per microphone
-    (``noise='white'``) or the sum of ``n_diffuse`` uncorrelated white plane waves
-    from uniformly random directions (``noise='diffuse'``).  SNR is the mic-averaged
+    (``noise='white'``), the sum of ``n_diffuse`` uncorrelated white plane waves
+    from uniformly random directions (``noise='diffuse'``), or a spherically isotropic
+    field (``noise='isotropic'``: the limit of infinitely many such plane waves, drawn
+    per bin with the coherence sin(w d_ij / c) / (w d_ij / c) between microphones i and j
+    at distance d_ij).  SNR is the mic-averaged
     signal power over noise power of that frame.
     """
     mic_xyz = np.asarray(mic_xyz, dtype=np.float64)
@@ -182,6 +201,8 @@ def plane_wave_frames(
     win = hann(N)
     k = np.arange(B, dtype=np.float64)
     out = np.empty((T, M, B), dtype=dtype)
+    if noise == "isotropic":
+        iso_mix = isotropic_mixing(mic_xyz, N, fs, c)
     chunk = 4096
     for t0 in range(0, T, chunk):
         t1 = min(T, t0 + chunk)
@@ -201,6 +222,8 @@ def plane_wave_frames(
             for j in range(n_diffuse):
                 d = (fs / c) * (dirs[:, j, :] @ mic_xyz.T)
                 nz += sp[:, j, None, :] * np.exp(2j * np.pi * d[:, :, None] * k[None, None, :] / N)
+        elif noise == "isotropic":
+            nz = np.einsum("kmj,njk->nmk", iso_mix, _windowed_spectra(rng, (n, M), N, win))
         else:
             raise ValueError(noise)
         ps = np.mean(np.abs(sig) ** 2, axis=(1, 2))
@@ -236,7 +259,7 @@ def workload(name: str, T: int | None = None, seed_offset: int = 0):
         src = random_directions(rng, T)[:, None, :]
         snr = rng.uniform(-5.0, 20.0, size=T)
         frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "white")
-    elif name == "array3d_q10242":      # 7-mic 3-D, Q=10242, 1-2 sources, diffuse noise 0-20 dB
+    elif name == "array3d_q10242":      # 7-mic 3-D, Q=10242, 1-2 sources, isotropic noise 0-20 dB
         rng = np.random.default_rng(SEED_BASE + 3 + seed_offset)
         mic, lvl, N = array_3d(), 5, 512
         T = 1 << 20 if T is None else T
@@ -247,8 +270,62 @@ def workload(name: str, T: int | None = None, seed_offset: int = 0):
         # duplicating the first direction (coherent sum keeps a single plane wave).
         src[nsrc == 1, 1, :] = src[nsrc == 1, 0, :]
         snr = rng.uniform(0.0, 20.0, size=T)
-        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "diffuse", n_diffuse=32)
+        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "isotropic")
     else:
         raise ValueError(f"unknown workload {name}")
     return dict(name=name, mic_xyz=mic, dirs=icosphere(lvl), fs=fs, c=c, N=N, delta=1e-5,
                 frames=frames, src_dirs=src, snr_db=snr)
+
+
+# --------------------------------------------------------------------------------------
+# Learned proposal: seeded parameters and training frames
+# --------------------------------------------------------------------------------------
+
+def mlp_params(rng: np.random.Generator, F: int, H1: int, H2: int, C: int) -> np.ndarray:
+    """A flat float32 parameter vector W1 [H1][F], b1, W2 [H2][H1], b2, W3 [C][H2], b3 with
+    weights drawn N(0, 2 / fan_in) and biases N(0, 0.05^2)."""
+    parts = []
+    for rows, cols in ((H1, F), (H2, H1), (C, H2)):
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / cols), size=rows * cols))
+        parts.append(rng.normal(0.0, 0.05, size=rows))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def training_frames(rng: np.random.Generator, mic_xyz: np.ndarray, T: int, N: int, fs: float, c: float,
+                    max_sources: int = 3, snr_range=(-5.0, 20.0)):
+    """T frames with 1..max_sources white plane-wave sources from uniform random directions
+    (a frame with fewer sources repeats its first direction), independent white noise at
+    a uniform random SNR.  Returns (frames, src_dirs (T, S, 3), n_sources (T,))."""
+    S = max_sources
+    src = random_directions(rng, T * S).reshape(T, S, 3)
+    ns = rng.integers(1, S + 1, size=T)
+    for s in range(1, S):
+        src[ns <= s, s, :] = src[ns <= s, 0, :]
+    snr = rng.uniform(snr_range[0], snr_range[1], size=T)
+    return plane_wave_frames(rng, mic_xyz, T, N, fs, c, src, snr, "white"), src, ns
+
+
+# --------------------------------------------------------------------------------------
+# Batched form: many independent streams
+# --------------------------------------------------------------------------------------
+
+def batched_streams(n: int, M_range=(4, 16), Q_choices=(642, 2562, 10242), N_choices=(256, 512, 1024),
+                    T_range=(50, 2000), snr_range=(-5.0, 20.0), seed_offset: int = 0):
+    """n streams, stream s drawn from its own generator keyed by (base seed + 2, s): M mics
+    uniform in a 5 cm-radius ball (>= 1 cm apart), Q from Q_choices, N from N_choices, T
+    uniform in T_range, one white plane-wave source per frame from a random direction, white
+    noise at a per-stream SNR uniform in snr_range.  fs 16 kHz, c 343 m/s, delta 1e-5."""
+    out = []
+    for s in range(n):
+        rng = np.random.default_rng([SEED_BASE + 2 + seed_offset, s])
+        M = int(rng.integers(M_range[0], M_range[1] + 1))
+        mic = array_random_ball(rng, M)
+        Q = int(rng.choice(Q_choices))
+        N = int(rng.choice(N_choices))
+        T = int(rng.integers(T_range[0], T_range[1] + 1))
+        snr = float(rng.uniform(*snr_range))
+        src = random_directions(rng, T)[:, None, :]
+        frames = plane_wave_frames(rng, mic, T, N, 16000.0, 343.0, src, np.full(T, snr), "white")
+        out.append(dict(mic_xyz=mic, dirs=icosphere(icosphere_level_for(Q)), N=N, fs=16000.0, c=343.0,
+                        delta=1e-5, frames=frames, src_dirs=src, snr_db=snr))
+    return out

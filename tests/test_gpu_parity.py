@@ -46,6 +46,24 @@ def _setup(name, T):
 CONFIGS = [("linear_q642", 100), ("planar_q2562", 777), ("array3d_q10242", 256)]
 
 
+def oracle_basis_in_library(d):
+    """The oracle's own V and D loaded into the library (through a basis file), so that a
+    single step of the CUDA path can be checked on the oracle's basis."""
+    if "ob_lib" not in d:
+        import os
+        import tempfile
+        import oracle_basis
+        wl = d["wl"]
+        fd, path = tempfile.mkstemp(suffix=".svdphat")
+        os.close(fd)
+        try:
+            oracle_basis.write(path, wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"], wl["delta"], d["ob"])
+            d["ob_lib"] = sp.load_basis(path)
+        finally:
+            os.remove(path)
+    return d["ob_lib"]
+
+
 def _sqdist(Dhat, Zq):
     """||Dhat_q - Zq_t||^2 for every (t, q), in blocks of frames (FP64)."""
     out = np.empty((Zq.shape[0], Dhat.shape[0]))
@@ -136,10 +154,12 @@ def test_svd_reduce_matches_oracle(name, T):
 @pytest.mark.parametrize("name,T", CONFIGS)
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 1e-4), ("bf16", 1e-3)])
 def test_project(name, T, prec, tol):
+    """Eq. 12 on the oracle's basis (Z depends on the phases of V's columns)."""
     d = _setup(name, T)
-    Zg = sp.project(d["b"], d["frames"], prec).cpu().numpy()
-    Zr = O.project(d["b"].V(), d["X"])   # the library's own basis: Z depends on V's phases
-    assert np.max(np.abs(Zg - Zr)) <= tol * np.sqrt(d["L"])
+    b = oracle_basis_in_library(d)
+    assert np.array_equal(b.V(), d["ob"]["V"])
+    Zg = sp.project(b, d["frames"], prec).cpu().numpy()
+    assert np.max(np.abs(Zg - d["Z"])) <= tol * np.sqrt(d["L"])
 
 
 @pytest.mark.parametrize("name,T", CONFIGS)
@@ -174,13 +194,14 @@ def test_localize_kdtree(name, T, prec):
     b = d["b"]
     idx, _, proj = sp.localize(b, d["frames"], "svd_kdtree", prec, score=False)
     idx = idx.cpu().numpy()
-    # exact search: the brute-force neighbour of the GPU's own query
+    # exact search: the brute-force neighbour (plain numpy here) of the GPU's own query
     Zg = sp.project(b, d["frames"], prec).cpu().numpy()
     D = b.D()
     Dhat = D / np.linalg.norm(D, axis=1, keepdims=True)
-    nn, d2 = O.nn_brute(Dhat, Zg)
     Zh = np.conj(Zg / np.linalg.norm(Zg, axis=1, keepdims=True))
     dist = _sqdist(Dhat, Zh)
+    nn = np.argmin(dist, axis=1)
+    d2 = dist[np.arange(len(nn)), nn]
     cls = d["cls"]
     dsec = np.where(cls[None, :] == cls[nn][:, None], np.inf, dist).min(axis=1)
     clear = dsec - d2 > 1e-5
