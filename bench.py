@@ -5,9 +5,15 @@ B = 257 bins), Q = 2562 icosphere directions, K from delta = 1e-5 (K = 48), 65,5
 per step with one white-noise plane-wave source per frame at SNR U(-5, 20) dB (synthetic).
 A step is one pass of Algorithm 1's online path over the batch: PHAT -> Z = V^H X ->
 exhaustive Re{D Z} argmax (FP16 tensor cores, then FP32 rescoring of every class within the
-FP16 rounding bound of the best) -> Y_qbar from the row of W (online step 4).  The STFT batch (943 MB) is larger than L2, so no flush is needed.
+FP16 rounding bound of the best) -> Y_qbar from the row of W (online step 4): three kernel
+launches.  The STFT batch (943 MB) is larger than L2, so no flush is needed.
+
+Extra keys (unless --no-extras): the same frames through FP32 SRP-PHAT, the FP32 / BF16
+paths and the k-d tree; the 3-D 7-mic array with Q = 10242 (exhaustive, learned proposal,
+k-d tree on 2^20 frames); 256 batched streams in one CUDA-graph launch.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec fp16|bf16]
+                [--frames T] [--no-extras] [--only array3d|batched] [--array3d-frames T]
 Under torchrun each rank localises its own 65,536 frames (weak scaling, no collective on the
 data path); rank 0 prints one JSON line.
 """
@@ -166,17 +172,17 @@ C4_UNIQUE, C4_REPEAT = 32768, 32
 LEARNED_N_TOP, LEARNED_THETA = 8, 0.2
 
 
-def bench_array3d(sp, I, torch):
+def bench_array3d(sp, I, torch, unique=C4_UNIQUE, repeat=C4_REPEAT):
     """The k-d tree and learned-proposal forms on the 3-D 7-mic array, Q = 10242 (level-5
     grid), K = 71: 1,048,576 frames per pass (32,768 unique frames of 1-2 white sources in
     isotropic noise at 0-20 dB, repeated 32 times on the device).  The proposal (level-3
     cells, 2K -> 256 -> 256 -> 642) is trained first, untimed, on 65,536 frames of 1-3
     sources the method labels itself."""
-    wl = I.workload("array3d_q10242", T=C4_UNIQUE, seed_offset=11)
+    wl = I.workload("array3d_q10242", T=unique, seed_offset=11)
     st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"])
     b = sp.svd_reduce(st, wl["delta"])
     uniq = torch.from_numpy(wl["frames"]).cuda()
-    frames = uniq.repeat(C4_REPEAT, 1, 1)
+    frames = uniq.repeat(repeat, 1, 1) if repeat > 1 else uniq
     T = frames.shape[0]
     rng = np.random.default_rng(I.SEED_BASE + 50)
     tr, _, _ = I.training_frames(rng, wl["mic_xyz"], 65536, wl["N"], wl["fs"], wl["c"])
@@ -209,7 +215,7 @@ def bench_array3d(sp, I, torch):
     del Z, zn2
     out = {
         "workload": f"array3d_q10242: 7-mic 3-D array, Q=10242, N=512, K={b.K}, {T} frames per pass "
-                    f"({C4_UNIQUE} unique x {C4_REPEAT}), 1-2 sources, isotropic noise 0-20 dB",
+                    f"({unique} unique x {repeat}), 1-2 sources, isotropic noise 0-20 dB",
         "svd_exhaustive_fp16_frames_per_s": T / t_exh * 1000,
         "svd_learned_fp16_frames_per_s": T / t_lrn * 1000,
         "svd_kdtree_fp16_frames_per_s": T / t_kd * 1000,
@@ -260,7 +266,7 @@ def bench_batched(sp, I, torch):
 
     def serial():   # FP32 where a basis has no tensor-core plan, as in the graph
         for b, f in zip(sb, sf):
-            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 144 else "fp16")
+            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 256 else "fp16")
     s_rate = _rate(serial, 3, total, torch)
     ks = sorted({b.K for b in bases})
     return {"workload": f"{N_STREAMS} streams, {total} frames, {N_CONFIGS} configurations (M 4-12, Q 642/2562, "
@@ -291,6 +297,10 @@ def main():
     ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16"])
     ap.add_argument("--frames", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the SRP / precision comparison lines")
+    ap.add_argument("--only", choices=["array3d", "batched"], default=None,
+                    help="run only one extra section and print its JSON (profiling runs)")
+    ap.add_argument("--array3d-frames", type=int, default=C4_UNIQUE,
+                    help="unique frames of the 3-D array section (repeated to 2^20 unless --only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -310,6 +320,12 @@ def main():
     __graft_entry__.build()
     import paper_1811_11785_gb300 as sp
     from paper_1811_11785_gb300 import inputs as I
+    if args.only is not None:
+        if args.only == "array3d":
+            print(json.dumps(bench_array3d(sp, I, torch, args.array3d_frames, 1)), flush=True)
+        else:
+            print(json.dumps(bench_batched(sp, I, torch)), flush=True)
+        return
 
     def lib_project(b, frames, prec, zout):
         rc = sp.lib().sp_project(b.handle, ctypes.c_void_p(frames.data_ptr()), frames.shape[0], sp.PREC[prec],
@@ -427,7 +443,7 @@ def main():
             other = "bf16" if args.prec == "fp16" else "fp16"
             extras[f"svd_{other}_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", other), 5)
             extras["svd_kdtree_fp16_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_kdtree", "fp16"), 3)
-            extras["array3d_q10242"] = bench_array3d(sp, I, torch)
+            extras["array3d_q10242"] = bench_array3d(sp, I, torch, args.array3d_frames, C4_REPEAT)
             extras["batched_256_streams"] = bench_batched(sp, I, torch)
 
         peak, peak_kind = _peaks()

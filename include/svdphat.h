@@ -258,7 +258,7 @@ int sp_set_wait_budget(long long iterations);
  * of frames): n independent streams, each with its own basis (array, grid, N, K), frames
  * and frame count, localised by one CUDA-graph launch whose branches run concurrently.
  * Each stream computes exactly what sp_localize computes for it (same kernels, same
- * results); where a basis has no tensor-core path (2K > 144 or M > 16) an FP16/BF16 request
+ * results); where a basis has no tensor-core path (2K > 256 or M > 16) an FP16/BF16 request
  * runs that stream in FP32.
  *
  * sp_batch_create: bases[i] (must outlive the plan), frames_dev[i] (device [T[i]][M][B]

@@ -80,7 +80,8 @@ constexpr int kGroupPairs = 24;       // pairs per stage group (3 atoms)
 constexpr int kAtomElems = 64;        // 16-bit elements per swizzle atom row
 constexpr int kAtomBytes = 128 * 128; // one 128-row atom
 constexpr int kGroupElems = 3 * kAtomElems;
-constexpr int kMaxN1 = 144;           // GEMM1 N limit of this shared-memory plan
+constexpr int kMaxN1 = 256;           // GEMM1 N limit (UMMA N <= 256)
+constexpr int kMaxN1Smem = 144;       // widest basis of the shared-memory A plan
 constexpr int kProdWarps = 16;
 constexpr int kProjThreads = 22 * 32; // 16 producer, 4 epilogue, 1 TMA, 1 MMA warps
 constexpr int kEpiWarp0 = 16, kTmaWarp = 20, kMmaWarp = 21;
@@ -148,6 +149,7 @@ struct ProjParams {
     const float2 *frames;
     int T, M, B, P, G, n_chunks;
     int n1, K, n_tiles;
+    int n_zbuf, z_cols, a_col0, n_aslot, n_vslot;   // tensor-memory plan of svd_proj_tm_kernel
     float inv_vscale;
     float2 *z_out;       // [T][K] complex64
     float *zn2_out;      // [T] ||Z||^2 or null
@@ -393,6 +395,280 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                                      idesc, (sl > 0 || k > 0) ? 1u : 0u);
                     }
                     ptx::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                ptx::mma_commit(&zfull[zb]);
+            }
+            ptx::mma_commit(drain);  // completes once every MMA issued above is done
+            ptx::mbar_wait(drain, 0, kDrainBudget);
+        }
+        __syncwarp();
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ------------------------------------------------------------ GEMM1, wide bases (2K > 144)
+// The same computation with the A operand in tensor memory instead of shared memory, which
+// leaves shared memory to the V stages a wide basis needs (up to 2K = 256 columns).  Tensor
+// memory: one Z accumulator of z_cols columns, then n_aslot A stages of 96 columns (128 frames
+// x 192 K-elements, two FP16/BF16 per column).  Producer warp w owns TMEM lane quarter w % 4
+// (frame rows 32 (w % 4) ..) and bin w / 4 of each 4-bin chunk and writes its cross spectra
+// with tcgen05.st; the MMA reads A from tensor memory and V from a ring of n_vslot
+// shared-memory stages fed by TMA.
+constexpr int kAStageCols = 3 * kAtomElems / 2;   // TMEM columns of one A stage (3 atoms)
+constexpr int kMaxASlots = 4, kMaxVSlots = 4;
+
+// MMAX: bound on the microphone count (EXACT: M == MMAX, known at compile time);
+// DEPTH: how many items of raw STFT values are held in registers ahead of use.
+//
+// Tensor memory: Z accumulators (n_zbuf buffers of z_cols columns) then n_aslot A stages of
+// 96 columns (128 frames x 192 K-elements, two FP16/BF16 per column).  Producer warp w owns
+// TMEM lane quarter w % 4 (frame rows 32 (w % 4) ..) and bin w / 4 of each 4-bin chunk, and
+// writes its cross spectra with tcgen05.st; the MMA reads A from tensor memory and V from a
+// ring of n_vslot shared-memory stages fed by TMA, so shared memory holds only V and the
+// rest of the SM's 228 KB stays L1 for the STFT loads.
+template <int BF16, int MMAX, bool EXACT, int DEPTH>
+__global__ void __launch_bounds__(kProjThreads, 1)
+    svd_proj_tm_kernel(const __grid_constant__ CUtensorMap tmap_v, const ProjParams prm) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n1 = prm.n1, n_as = prm.n_aslot, n_vs = prm.n_vslot, n_zb = prm.n_zbuf;
+    const int b_stage = 3 * n1 * 128;
+    const int off_bar = n_vs * b_stage;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + off_bar);
+    uint64_t *full_a = bars, *empty_a = bars + kMaxASlots;
+    uint64_t *full_v = bars + 2 * kMaxASlots, *empty_v = full_v + kMaxVSlots;
+    uint64_t *zfull = empty_v + kMaxVSlots, *zempty = zfull + 2, *drain = zempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(drain + 2);
+    const long long budget = g_wait_budget;
+
+    if (tid == 0) {
+        for (int i = 0; i < kMaxASlots; ++i) {
+            ptx::mbar_init(&full_a[i], kProdWarps);
+            ptx::mbar_init(&empty_a[i], 1);
+        }
+        for (int i = 0; i < kMaxVSlots; ++i) {
+            ptx::mbar_init(&full_v[i], 1);
+            ptx::mbar_init(&empty_v[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&zfull[i], 1);
+            ptx::mbar_init(&zempty[i], 128);
+        }
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == kTmaWarp && lane == 0) ptx::prefetch_tmap(&tmap_v);
+    if (warp == kMmaWarp) {
+        ptx::tmem_alloc(tmem_slot, 512);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int stages_per_tile = prm.n_chunks * prm.G;
+    const int my_tiles = prm.n_tiles > (int)blockIdx.x ? (prm.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        atomicOr(&g_status, 1);
+    };
+
+    if (warp < kProdWarps) {
+        // -------- producers: PHAT of (frame row r, bin b) of every chunk of every tile.
+        // The STFT stream of this thread is a flat sequence of items (local tile, chunk); the
+        // raw values of item j + DEPTH are in flight while item j is normalised and written.
+        // With EXACT, the pair layout (P, groups, slots) is known at compile time.
+        constexpr int NPAIR = MMAX * (MMAX - 1) / 2;
+        constexpr PairTab<MMAX> tab = make_pair_tab<MMAX>();
+        const int M = EXACT ? MMAX : prm.M;
+        const int P = EXACT ? NPAIR : prm.P;
+        const int G = EXACT ? (NPAIR + kGroupPairs - 1) / kGroupPairs : prm.G;
+        const int q4 = warp & 3, b = warp >> 2;
+        const int f = q4 * 32 + lane;                      // frame row = TMEM lane
+        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)prm.a_col0 + (uint32_t)b;
+        const int n_chunks = prm.n_chunks;
+        const size_t frame_elems = (size_t)M * prm.B;
+        int ld_li = 0, ld_c = 0;
+        const float2 *ld_fr = prm.frames;
+        bool ld_live = false;
+        auto ld_seek_tile = [&]() {
+            const long long frame = (long long)((int)blockIdx.x + ld_li * (int)gridDim.x) * 128 + f;
+            ld_live = ld_li < my_tiles && frame < prm.T;
+            ld_fr = prm.frames + (ld_live ? (size_t)frame * frame_elems : 0);
+        };
+        float2 raw[DEPTH][MMAX];
+        auto load_next = [&](float2 (&dst)[MMAX]) {
+            const int k = ld_c * kChunkBins + b;
+            const bool ok = ld_live && k < prm.B;
+#pragma unroll
+            for (int m = 0; m < MMAX; ++m)
+                dst[m] = (ok && m < M) ? ld_stream(ld_fr + (size_t)m * prm.B + k) : make_float2(0.f, 0.f);
+            if (++ld_c == n_chunks) {
+                ld_c = 0;
+                ++ld_li;
+                ld_seek_tile();
+            }
+        };
+        ld_seek_tile();
+        const int n_items = my_tiles * n_chunks;
+        int st = 0;  // stage counter
+        auto step = [&](float2 (&cur)[MMAX]) -> bool {
+            float2 xh[MMAX];
+#pragma unroll
+            for (int m = 0; m < MMAX; ++m) {
+                const float2 v = cur[m];
+                const float mag2 = v.x * v.x + v.y * v.y;
+                const float r = mag2 < 1e-30f ? 0.f : rsqrtf(mag2);
+                xh[m] = make_float2(v.x * r, v.y * r);
+            }
+            load_next(cur);
+            for (int g = 0; g < G; ++g, ++st) {
+                const int s = st % n_as;
+                const uint32_t par = ((st / n_as) & 1) ^ 1;
+                if (ptx::warp_flag(abort_flag)) return false;
+                if (!ptx::mbar_wait_warp(&empty_a[s], par, budget)) {
+                    if (lane == 0) give_up();
+                    return false;
+                }
+                ptx::tc_fence_after();
+                const uint32_t col0 = lane_base + (uint32_t)(s * kAStageCols);
+                const int p_lo = g * kGroupPairs;
+                const int npg = min(kGroupPairs, P - p_lo);
+#pragma unroll
+                for (int pp = 0; pp < NPAIR; ++pp) {
+                    const int i = tab.i[pp], jj = tab.j[pp];
+                    if (jj < M) {
+                        const int p = i * M - ((i * (i + 1)) >> 1) + (jj - i - 1);
+                        const int pl = p - p_lo;
+                        if (pl >= 0 && pl < npg) {
+                            const float2 a0 = xh[i], b0 = xh[jj];
+                            ptx::tmem_st1(col0 + (uint32_t)(pl * 4),
+                                          pack2<BF16>(a0.x * b0.x + a0.y * b0.y, a0.y * b0.x - a0.x * b0.y));
+                        }
+                    }
+                }
+                if (npg & 1) ptx::tmem_st1(col0 + (uint32_t)(npg * 4), 0u);   // partner of an odd last pair
+                ptx::tmem_wait_st();
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&full_a[s]);
+            }
+            return true;
+        };
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) load_next(raw[d]);
+        bool ok = true;
+        for (int j = 0; j < n_items && ok; j += DEPTH) {
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d)
+                if (ok && j + d < n_items) ok = step(raw[d]);
+        }
+    } else if (warp < kEpiWarp0 + 4) {
+        // -------- epilogue: Z of each finished tile, TMEM -> FP32 global
+        const int q4 = warp - kEpiWarp0;   // TMEM lane quarter of this warp (warp % 4)
+        const int r = q4 * 32 + lane;      // frame row within the tile
+        for (int li = 0; li < my_tiles; ++li) {
+            const int zb = n_zb == 2 ? (li & 1) : 0;
+            const uint32_t zpar = n_zb == 2 ? ((li >> 1) & 1) : (li & 1);
+            if (ptx::warp_flag(abort_flag)) break;
+            if (!ptx::mbar_wait_warp(&zfull[zb], zpar, budget)) {
+                if (lane == 0) give_up();
+                break;
+            }
+            ptx::tc_fence_after();
+            const long long frame = (long long)((int)blockIdx.x + li * (int)gridDim.x) * 128 + r;
+            float2 *zo = prm.z_out + (size_t)(frame < prm.T ? frame : 0) * prm.K;
+            float zn2 = 0.f;
+            for (int c0 = 0; c0 < n1; c0 += 32) {
+                float v[32];
+                ptx::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(zb * prm.z_cols + c0), v);
+                if (frame < prm.T) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const int kk = (c0 + i) >> 1;
+                        if (kk < prm.K) {
+                            const float2 z = make_float2(v[i] * prm.inv_vscale, v[i + 1] * prm.inv_vscale);
+                            zo[kk] = z;
+                            zn2 = fmaf(z.x, z.x, fmaf(z.y, z.y, zn2));
+                        }
+                    }
+                }
+            }
+            if (prm.zn2_out && frame < prm.T) prm.zn2_out[frame] = zn2;
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&zempty[zb]);
+        }
+    } else if (warp == kTmaWarp) {
+        if (lane == 0) {
+            int issued = -1;
+            const int n_stages = my_tiles * stages_per_tile;
+            for (int st = 0; st < n_stages; ++st) {
+                const int s = st % n_vs;
+                if (*abort_flag) break;
+                if (!ptx::mbar_wait(&empty_v[s], ((st / n_vs) & 1) ^ 1, budget)) {
+                    give_up();
+                    break;
+                }
+                const int sl = st % stages_per_tile;
+                const int g = sl % prm.G;
+                const int npg = min(kGroupPairs, prm.P - g * kGroupPairs);
+                const int atoms = (((npg + 1) >> 1) + 3) >> 2;
+                ptx::mbar_arrive_expect_tx(&full_v[s], (uint32_t)(atoms * n1 * 128));
+                uint8_t *Bs = smem + s * b_stage;
+                for (int a = 0; a < atoms; ++a)
+                    ptx::tma_load_2d(Bs + a * n1 * 128, &tmap_v, &full_v[s], sl * kGroupElems + a * kAtomElems, 0);
+                issued = st;
+            }
+            for (int st = max(0, issued - n_vs + 1); st <= issued; ++st)
+                ptx::mbar_wait(&full_v[st % n_vs], (st / n_vs) & 1, kDrainBudget);
+        }
+        __syncwarp();
+    } else {  // kMmaWarp
+        if (lane == 0) {
+            const uint32_t idesc = ptx::idesc_f16(128, n1, BF16);
+            int st = 0;
+            for (int li = 0; li < my_tiles; ++li) {
+                const int zb = n_zb == 2 ? (li & 1) : 0;
+                const uint32_t zpar = (n_zb == 2 ? ((li >> 1) & 1) : (li & 1)) ^ 1;
+                if (*abort_flag) break;
+                if (!ptx::mbar_wait(&zempty[zb], zpar, budget)) {
+                    give_up();
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(zb * prm.z_cols);
+                bool ok = true;
+                for (int sl = 0; sl < stages_per_tile; ++sl, ++st) {
+                    const int sa = st % n_as, sv = st % n_vs;
+                    if (*abort_flag || !ptx::mbar_wait(&full_a[sa], (st / n_as) & 1, budget) ||
+                        !ptx::mbar_wait(&full_v[sv], (st / n_vs) & 1, budget)) {
+                        if (!*abort_flag) give_up();
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const int g = sl % prm.G;
+                    const int npg = min(kGroupPairs, prm.P - g * kGroupPairs);
+                    const int steps = (npg + 1) >> 1;
+                    const uint32_t a_tmem = tmem + (uint32_t)(prm.a_col0 + sa * kAStageCols);
+                    const uint32_t b_base = ptx::smem_u32(smem + sv * b_stage);
+                    for (int k = 0; k < steps; ++k) {
+                        const uint32_t bo = (k >> 2) * n1 * 128 + (k & 3) * 32;
+                        ptx::mma_f16_ts(d_tmem, a_tmem + (uint32_t)(k * 8), ptx::sw128_desc(b_base + bo), idesc,
+                                        (sl > 0 || k > 0) ? 1u : 0u);
+                    }
+                    ptx::mma_commit(&empty_a[sa]);
+                    ptx::mma_commit(&empty_v[sv]);
                 }
                 if (!ok) break;
                 ptx::mma_commit(&zfull[zb]);
@@ -777,7 +1053,7 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "tensor-core path supports 2K <= 144 and M <= 16 (use SP_PREC_FP32)");
+             "tensor-core path supports 2K <= 256 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
     ProjParams p;
@@ -794,23 +1070,48 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     p.inv_vscale = 1.f / b->v_scale;
     p.z_out = (float2 *)z_out;
     p.zn2_out = zn2_out;
-    const int smem = 2 * 3 * kAtomBytes + 2 * 3 * t.n1 * 128 + 128 + 1024;
-    SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
+    const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
     // variants: exactly 7 microphones (the Table 2 arrays), up to 8, up to 16
     const int which = bf * 3 + (p.M == 7 ? 0 : p.M <= 8 ? 1 : 2);
-    void (*const kerns[6])(CUtensorMap, ProjParams) = {
-        svd_proj_kernel<0, 7, true, 2>, svd_proj_kernel<0, 8, false, 2>, svd_proj_kernel<0, 16, false, 1>,
-        svd_proj_kernel<1, 7, true, 2>, svd_proj_kernel<1, 8, false, 2>, svd_proj_kernel<1, 16, false, 1>};
-    auto kern = kerns[which];
-    static bool attr[6] = {false, false, false, false, false, false};
-    if (!attr[which]) {
-        SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-        attr[which] = true;
+    if (t.n1 <= kMaxN1Smem) {
+        // A operand in shared memory: two stages of A (48 KB) and V (3 atoms of n1 rows)
+        const int smem = 2 * 3 * kAtomBytes + 2 * 3 * t.n1 * 128 + 128 + 1024;
+        SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
+        void (*const kerns[6])(CUtensorMap, ProjParams) = {
+            svd_proj_kernel<0, 7, true, 2>, svd_proj_kernel<0, 8, false, 2>, svd_proj_kernel<0, 16, false, 1>,
+            svd_proj_kernel<1, 7, true, 2>, svd_proj_kernel<1, 8, false, 2>, svd_proj_kernel<1, 16, false, 1>};
+        auto kern = kerns[which];
+        static bool attr[6] = {false, false, false, false, false, false};
+        if (!attr[which]) {
+            SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+            attr[which] = true;
+        }
+        // at least 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM
+        const int smem_launch = std::max(smem, 120 * 1024);
+        kern<<<grid, kProjThreads, smem_launch, s>>>(maps->v[bf], p);
+    } else {
+        // A operand in tensor memory: one Z buffer, then A stages; shared memory holds V only
+        p.z_cols = (t.n1 + 31) / 32 * 32;
+        p.n_zbuf = 1;
+        p.a_col0 = p.z_cols;
+        p.n_aslot = std::min(kMaxASlots, (512 - p.a_col0) / kAStageCols);
+        const int b_stage = 3 * t.n1 * 128;
+        p.n_vslot = std::min(kMaxVSlots, (200 * 1024) / b_stage);
+        SP_CHECK(p.n_aslot >= 2 && p.n_vslot >= 2, SP_ENOTIMPL, "tensor-core plan: too few pipeline stages");
+        const int smem = p.n_vslot * b_stage + 256 + 1024;
+        SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
+        void (*const kerns[6])(CUtensorMap, ProjParams) = {
+            svd_proj_tm_kernel<0, 7, true, 2>, svd_proj_tm_kernel<0, 8, false, 2>,
+            svd_proj_tm_kernel<0, 16, false, 1>, svd_proj_tm_kernel<1, 7, true, 2>,
+            svd_proj_tm_kernel<1, 8, false, 2>, svd_proj_tm_kernel<1, 16, false, 1>};
+        auto kern = kerns[which];
+        static bool attr[6] = {false, false, false, false, false, false};
+        if (!attr[which]) {
+            SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+            attr[which] = true;
+        }
+        kern<<<grid, kProjThreads, std::max(smem, 120 * 1024), s>>>(maps->v[bf], p);
     }
-    // at least 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM
-    const int smem_launch = std::max(smem, 120 * 1024);
-    const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
-    kern<<<grid, kProjThreads, smem_launch, s>>>(maps->v[bf], p);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
@@ -820,7 +1121,7 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "tensor-core path supports 2K <= 144 and M <= 16 (use SP_PREC_FP32)");
+             "tensor-core path supports 2K <= 256 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
     ScanParams p;

@@ -271,6 +271,13 @@ def workload(name: str, T: int | None = None, seed_offset: int = 0):
         src[nsrc == 1, 1, :] = src[nsrc == 1, 0, :]
         snr = rng.uniform(0.0, 20.0, size=T)
         frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "isotropic")
+    elif name == "ball12_q642":         # 12 mics in a 5 cm-radius ball, Q=642, N=512: a wide basis
+        rng = np.random.default_rng([SEED_BASE + 7, 1])
+        mic, lvl, N = array_random_ball(rng, 12), 3, 512
+        T = 300 if T is None else T
+        src = random_directions(rng, T)[:, None, :]
+        snr = rng.uniform(-5.0, 20.0, size=T)
+        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "white")
     else:
         raise ValueError(f"unknown workload {name}")
     return dict(name=name, mic_xyz=mic, dirs=icosphere(lvl), fs=fs, c=c, N=N, delta=1e-5,

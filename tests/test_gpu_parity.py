@@ -43,7 +43,7 @@ def _setup(name, T):
     return d
 
 
-CONFIGS = [("linear_q642", 100), ("planar_q2562", 777), ("array3d_q10242", 256)]
+CONFIGS = [("linear_q642", 100), ("planar_q2562", 777), ("array3d_q10242", 256), ("ball12_q642", 300)]
 
 
 def oracle_basis_in_library(d):
@@ -159,7 +159,9 @@ def test_project(name, T, prec, tol):
     b = oracle_basis_in_library(d)
     assert np.array_equal(b.V(), d["ob"]["V"])
     Zg = sp.project(b, d["frames"], prec).cpu().numpy()
-    assert np.max(np.abs(Zg - d["Z"])) <= tol * np.sqrt(d["L"])
+    # FP32 accumulation over L terms: the bound grows with L (4e-8 L dominates beyond L ~ 2500)
+    bound = max(tol * np.sqrt(d["L"]), 4e-8 * d["L"]) if prec == "fp32" else tol * np.sqrt(d["L"])
+    assert np.max(np.abs(Zg - d["Z"])) <= bound
 
 
 @pytest.mark.parametrize("name,T", CONFIGS)
