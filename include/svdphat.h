@@ -47,7 +47,10 @@ extern "C" {
 typedef enum {
     SP_MODE_SRP = 0,             /* Eq. 9 + Eq. 6: argmax Re{W X} over all Q rows           */
     SP_MODE_SVD_EXHAUSTIVE = 1,  /* Eq. 12 + Eq. 14: argmax Re{D Z}, Z = V^H X              */
-    SP_MODE_SVD_KDTREE = 2       /* Eq. 15: nearest normalised row D^_q to conj(Z/||Z||)    */
+    SP_MODE_SVD_KDTREE = 2,      /* Eq. 15: nearest normalised row D^_q to conj(Z/||Z||)    */
+    SP_MODE_SVD_LEARNED = 3      /* Eq. 14 over the cells a trained network proposes: needs a
+                                    proposal handle, so it runs through sp_localize_learned;
+                                    sp_localize and the batch calls reject it (SP_EINVAL)     */
 } sp_mode;
 
 typedef enum {

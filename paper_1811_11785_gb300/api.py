@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-MODE = {"srp": 0, "svd_exhaustive": 1, "svd_kdtree": 2}
+MODE = {"srp": 0, "svd_exhaustive": 1, "svd_kdtree": 2, "svd_learned": 3}
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 STEER_MATERIALIZE_W = 1
 

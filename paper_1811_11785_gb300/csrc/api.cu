@@ -298,6 +298,8 @@ int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
             }
             break;
         }
+        case SP_MODE_SVD_LEARNED:
+            return fail(SP_EINVAL, "SP_MODE_SVD_LEARNED needs a proposal: call sp_localize_learned");
         default:
             return fail(SP_EINVAL, "sp_localize: bad mode");
     }

@@ -111,6 +111,7 @@ struct sp_steering {
     sp::DevBuf tau;                     // Q x P double
     sp::DevBuf d_mic;                   // M x 3 double
     sp::DevBuf d_dirs;                  // Q x 3 double (unit directions, for step 4)
+    sp::DevBuf step4_tab;               // Q x M float4: d_m/N (hi, lo), 64-bin step phasor
     sp::DevBuf W;                       // Q x L complex64 (optional)
     bool has_w = false;
     mutable sp::DevBuf work;            // workspace for SRP calls on this handle

@@ -56,6 +56,25 @@ __global__ void w_kernel(const double *__restrict__ tau, int Q, int P, int B, in
     W[idx] = make_float2((float)co, (float)s);
 }
 
+// Per direction q and microphone m, for online step 4: d_m / N in turns per bin, split as
+// float hi + lo (d_m = fs/c r_m . u_q in FP64), and the phasor exp(-2 pi i 64 d_m / N) of a
+// 64-bin step.  Computed once here so that the step-4 kernel does no FP64 work per frame.
+__global__ void step4_table_kernel(const double *__restrict__ mic, const double *__restrict__ unit, int Q, int M,
+                                   double g, double inv_n, float4 *__restrict__ tab) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Q * M) return;
+    const int q = (int)(idx / M), m = (int)(idx % M);
+    const double d = g * ((mic[3 * m] * unit[3 * q] + mic[3 * m + 1] * unit[3 * q + 1]) + mic[3 * m + 2] * unit[3 * q + 2]);
+    const double e = d * inv_n;
+    const float hi = (float)e;
+    const float lo = (float)(e - (double)hi);
+    const float p1 = 64.f * hi;
+    const float r1 = (p1 - rintf(p1)) + 64.f * lo;
+    float ss, sc;
+    sincospif(-2.f * r1, &ss, &sc);
+    tab[idx] = make_float4(hi, lo, sc, ss);
+}
+
 int launch_tau(const sp_steering *st, cudaStream_t s) {
     sp_steering *m = const_cast<sp_steering *>(st);
     SP_TRY(m->tau.reserve((size_t)st->Q * st->P * 8));
@@ -73,6 +92,14 @@ int launch_tau(const sp_steering *st, cudaStream_t s) {
         m->d_mic.as<double>(), d_dirs_in.as<double>(), d_pairs.as<int>(), d_pairs.as<int>() + st->P,
         st->Q, st->P, st->fs, st->c, m->tau.as<double>(), m->d_dirs.as<double>());
     SP_CUDA(cudaGetLastError());
+    {
+        const long long nm = (long long)st->Q * st->M;
+        SP_TRY(m->step4_tab.reserve((size_t)nm * 16));
+        step4_table_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(
+            m->d_mic.as<double>(), m->d_dirs.as<double>(), st->Q, st->M, st->fs / st->c, 1.0 / (double)st->N,
+            m->step4_tab.as<float4>());
+        SP_CUDA(cudaGetLastError());
+    }
     SP_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed on return
     return SP_OK;
 }

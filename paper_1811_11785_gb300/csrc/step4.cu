@@ -29,8 +29,7 @@ struct Step4Params {
     const float2 *frames;
     int T, M, B, n_pairs;
     unsigned pair_bytes;   // 16 M B
-    double inv_n, g;
-    const double *unit, *mic;
+    const float4 *tab;     // [Q][M]: d_m / N as float hi + lo, 64-bin step phasor (cos, sin)
     const int32_t *idx;
     float *score;
     int *status;
@@ -116,17 +115,15 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
         if (t < prm.T) q = prm.idx[t];
         if (q >= 0) {
             const float2 *fr = whole ? smem_frame : prm.frames + (size_t)t * M * B;
-            // lane m: d_m / N (split into two floats) and the 64-bin step phasor
+            // lane m: d_m / N (split into two floats) and the 64-bin step phasor, from the
+            // per-direction table built with the steering matrix
             float my_hi = 0.f, my_lo = 0.f, my_sc = 1.f, my_ss = 0.f;
             if (lane < M) {
-                const double d = prm.g * ((prm.mic[3 * lane] * prm.unit[3 * q] + prm.mic[3 * lane + 1] * prm.unit[3 * q + 1]) +
-                                          prm.mic[3 * lane + 2] * prm.unit[3 * q + 2]);
-                const double e = d * prm.inv_n;
-                my_hi = (float)e;
-                my_lo = (float)(e - (double)my_hi);
-                const float p1 = 64.f * my_hi;
-                const float r1 = (p1 - rintf(p1)) + 64.f * my_lo;
-                sincospif(-2.f * r1, &my_ss, &my_sc);
+                const float4 e = __ldg(prm.tab + (size_t)q * M + lane);
+                my_hi = e.x;
+                my_lo = e.y;
+                my_sc = e.z;
+                my_ss = e.w;
             }
             float2 ph[MMAX], stp[MMAX];
             const int k_first = 32 * gh + lane;
@@ -196,10 +193,7 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
     p.B = st->B;
     p.n_pairs = (T + 1) / 2;
     p.pair_bytes = pair_bytes;
-    p.inv_n = 1.0 / (double)st->N;
-    p.g = st->fs / st->c;
-    p.unit = st->d_dirs.as<double>();
-    p.mic = st->d_mic.as<double>();
+    p.tab = st->step4_tab.as<float4>();
     p.idx = idx;
     p.score = score;
     SP_TRY(device_status_ptr(&p.status));

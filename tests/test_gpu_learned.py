@@ -249,3 +249,10 @@ def test_trained_network_gain():
     for key, max_fb in (((8, 0.2), 0.05), ((8, 0.4), 0.3)):
         fbf, agree = table[key]
         assert agree >= 0.995 and fbf <= max_fb, (key, fbf, agree)
+
+
+def test_learned_mode_needs_a_proposal():
+    d = _ctx()
+    with pytest.raises(sp.SvdPhatError) as e:
+        sp.localize(d["b"], d["frames"], "svd_learned", "fp16")
+    assert e.value.code == -1
