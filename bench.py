@@ -134,6 +134,16 @@ def oracle_sample(wl, n_frames: int, seed: int = 7):
     return n_frames / dt, dt, sel, idx, Y, O.direction_classes(tau)
 
 
+def arm_config(K: int, T: int) -> dict:
+    """The config of the measured workload, the same for both arms."""
+    return {"workload": f"{WORKLOAD}: 7-mic planar array, Q=2562, N=512, K={K}, "
+                        f"{T} frames/step/GPU, SNR U(-5,20) dB",
+            "frames_per_step": T, "Q": 2562, "M": 7, "N": 512, "K": K,
+            "mode": "svd_exhaustive (FP16/BF16 scan + FP32 rescoring of every class within the "
+                    "rounding bound) + online step 4",
+            "l2": "inputs (943 MB STFT) larger than L2; no flush"}
+
+
 def _cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -156,14 +166,17 @@ def run_reference(args):
         r, dt, *_ = oracle_sample(wl, n, seed=100 + s)
         rates.append(r)
         secs.append(dt)
+    import oracle as O
+    tau = O.tdoa_farfield(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"])
+    K = O.svd_basis(O.steering(tau, wl["N"]), wl["delta"])["K"]
     v = n * len(secs) / sum(secs)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (FP64 oracle on host cores)",
-                                            "frames_per_step": n, "Q": 2562, "M": 7, "N": 512, "K": 48},
+            "data": "synthetic", "config": arm_config(K, args.frames),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-                             "sample": f"{n} frames per step drawn from an 8192-frame batch of the workload"},
+                             "sample": f"{n} frames per step (FP64 on the host cores) drawn from an 8192-frame "
+                                       "batch of the workload"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -455,12 +468,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: 7-mic planar array, Q=2562, N=512, K={b.K}, "
-                                   f"{T} frames/step/GPU, SNR U(-5,20) dB",
-                       "frames_per_step": T, "Q": st.Q, "M": st.M, "N": st.N, "K": b.K,
-                       "mode": "svd_exhaustive (FP16/BF16 scan + FP32 rescoring of every class within the "
-                               "rounding bound) + online step 4",
-                       "l2": "inputs (943 MB STFT) larger than L2; no flush"},
+            "config": arm_config(b.K, T),
             "agreement_vs_oracle": agree, "agreement_sample_frames": int(len(sel)),
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
