@@ -131,6 +131,7 @@ def oracle_sample(wl, n_frames: int, seed: int = 7):
     idx, _ = O.argmax_lowest(Y)
     O.score_row(tau, idx, X, wl["N"])
     dt = time.perf_counter() - t0
+    oracle_sample.last = dict(tau=tau, X=X, L=W.shape[1])   # for error statistics (untimed)
     return n_frames / dt, dt, sel, idx, Y, O.direction_classes(tau)
 
 
@@ -439,6 +440,12 @@ def main():
         rate, dt, sel, ref, Y, cls = oracle_sample(wl, 2048)
         gi = idx.cpu().numpy()[sel]
         agree = float(np.mean(cls[gi] == cls[ref]))
+        # score errors against the FP64 oracle on the same sample, in units of L (|Y| <= L)
+        import oracle as O
+        last = oracle_sample.last
+        Lr = float(last["L"])
+        proj_err = float(np.max(np.abs(proj.cpu().numpy()[sel] - Y[np.arange(len(sel)), gi]))) / Lr
+        s4_err = float(np.max(np.abs(score.cpu().numpy()[sel] - O.score_row(last["tau"], gi, last["X"], wl["N"])))) / Lr
         if not args.no_extras:
             # plain FP32 SRP-PHAT (the reference form) and the other precisions, same frames
             def rate_of(fn, n):
@@ -470,6 +477,7 @@ def main():
             "data": "synthetic",
             "config": arm_config(b.K, T),
             "agreement_vs_oracle": agree, "agreement_sample_frames": int(len(sel)),
+            "score_error_vs_oracle": {"search_score_max_over_L": proj_err, "step4_score_max_over_L": s4_err},
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": TRAFFIC_PER_FRAME and TRAFFIC_PER_FRAME * T,

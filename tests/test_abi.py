@@ -118,3 +118,19 @@ def test_load_basis_rejects_missing_file_and_null_arguments(lib, tmp_path):
     assert lib.sp_load_basis(b"x", 4, ctypes.byref(out), None) == api.SP_EINVAL
     assert lib.sp_save_basis(None, b"x") == api.SP_EINVAL
     assert lib.sp_basis_steering(None, ctypes.byref(out)) == api.SP_EINVAL
+
+
+def test_batch_and_proposal_calls_reject_bad_arguments(lib):
+    out = ctypes.c_void_p()
+    assert lib.sp_batch_create(0, None, None, None, 1, 1, None, None, None, 0, None, ctypes.byref(out)) == api.SP_EINVAL
+    assert lib.sp_batch_create(1, None, None, None, 1, 1, None, None, None, 0, None, None) == api.SP_EINVAL
+    assert lib.sp_batch_create(1, None, None, None, 1, 1, None, None, None, 0, None, ctypes.byref(out)) == api.SP_EINVAL
+    assert lib.sp_batch_run(None, None) == api.SP_EINVAL
+    assert lib.sp_batch_info(None, None, None, None, None) == api.SP_EINVAL
+    lib.sp_batch_destroy(None)
+    assert lib.sp_proposal_create(None, None, 642, 256, 256, 0, ctypes.byref(out)) == api.SP_EINVAL
+    assert lib.sp_proposal_create(None, None, 642, 256, 256, 0, None) == api.SP_EINVAL
+    assert lib.sp_localize_learned(None, None, 4, 1, 4, ctypes.c_float(0.5), None, None, None, None, None) == api.SP_EINVAL
+    assert lib.sp_proposal_dims(None, None, None, None, None, None) == api.SP_EINVAL
+    assert lib.sp_proposal_train_step(None, None, None, None, 4, ctypes.c_float(1e-3), None, None) == api.SP_EINVAL
+    lib.sp_proposal_destroy(None)
