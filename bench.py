@@ -40,10 +40,10 @@ UNIT = "frames/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes read + written per frame by svd_proj_kernel, from one ncu capture of this
-# version of the kernel on 19,456 frames of the same workload (311.2 MB / 19,456), scaled to
+# version of the kernel on 19,456 frames of the same workload (311.3 MB / 19,456), scaled to
 # a launch by the frame count (traffic grows in proportion to frames).  Set to None when the
 # kernel changes until it is captured again.
-TRAFFIC_PER_FRAME = 15994.0
+TRAFFIC_PER_FRAME = 16001.0
 
 
 def _peaks():

@@ -88,3 +88,16 @@ def test_batch_mixes_tensor_core_and_fp32_streams():
         prec = "fp32" if i in big else "fp16"
         ref = sp.localize(bases[i], frames[i], "svd_exhaustive", prec)
         assert torch.equal(bt.idx[k], ref[0])
+
+
+@pytest.mark.parametrize("mode,prec", [("svd_kdtree", "fp16"), ("svd_exhaustive", "bf16")])
+def test_batch_other_modes_equal_per_stream(mode, prec):
+    wls, bases, frames = _streams()
+    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 256][:6]
+    bt = sp.Batch([bases[i] for i in sel], [frames[i] for i in sel], mode, prec)
+    bt.run()
+    torch.cuda.synchronize()
+    sp.check_status()
+    for k, i in enumerate(sel):
+        idx, score, proj = sp.localize(bases[i], frames[i], mode, prec)
+        assert torch.equal(bt.idx[k], idx) and torch.equal(bt.score[k], score)

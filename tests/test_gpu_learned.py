@@ -256,3 +256,14 @@ def test_learned_mode_needs_a_proposal():
     with pytest.raises(sp.SvdPhatError) as e:
         sp.localize(d["b"], d["frames"], "svd_learned", "fp16")
     assert e.value.code == -1
+
+
+def test_bf16_learned_fallback_equals_exhaustive():
+    """Every frame falling back (theta > 1) gives exactly the exhaustive BF16 result."""
+    d = _ctx()
+    p = sp.Proposal(d["b"], d["cells"], seed=3)
+    li, ls, _, fb = p.localize(d["frames"], "bf16", n_top=4, theta=2.0)
+    ei, es, _ = sp.localize(d["b"], d["frames"], "svd_exhaustive", "bf16")
+    torch.cuda.synchronize()
+    assert bool(fb.all())
+    assert torch.equal(li, ei) and torch.equal(ls, es)
