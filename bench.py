@@ -145,6 +145,14 @@ def arm_config(K: int, T: int) -> dict:
             "l2": "inputs (943 MB STFT) larger than L2; no flush"}
 
 
+def clocks_sm_mhz(clk) -> float | None:
+    """The median SM clock the Clocks sampler saw, if any."""
+    try:
+        return float(clk["sm_mhz"]) if clk and clk.get("sm_mhz") else None
+    except Exception:
+        return None
+
+
 def _cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -280,7 +288,7 @@ def bench_batched(sp, I, torch):
 
     def serial():   # FP32 where a basis has no tensor-core plan, as in the graph
         for b, f in zip(sb, sf):
-            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 256 else "fp16")
+            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 320 else "fp16")
     s_rate = _rate(serial, 3, total, torch)
     ks = sorted({b.K for b in bases})
     return {"workload": f"{N_STREAMS} streams, {total} frames, {N_CONFIGS} configurations (M 4-12, Q 642/2562, "
@@ -459,6 +467,16 @@ def main():
                 torch.cuda.synchronize()
                 return T * n / (a.elapsed_time(z) / 1000)
             extras["srp_fp32_frames_per_s"] = rate_of(lambda: sp.localize_srp(st, frames), 2)
+            # plain SRP-PHAT is FP32-ALU bound: 4 Q L flops per frame (Eq. 9) against the FP32 FMA
+            # peak from the unit counts (128 FP32 lanes per SM, 2 flops per FMA) and the SM clock
+            sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+            sm_mhz = clocks_sm_mhz(clk) or 2070.0
+            alu_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+            srp_tflops = extras["srp_fp32_frames_per_s"] * 4.0 * st.Q * st.L / 1e12
+            extras["srp_fp32_roofline"] = {"bound": "alu", "achieved": srp_tflops, "peak": alu_peak,
+                                           "unit": "TFLOP/s", "frac": srp_tflops / alu_peak,
+                                           "peak_source": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 flops x "
+                                                          f"{sm_mhz:.0f} MHz (median SM clock of the timed region)"}
             extras["svd_fp32_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", "fp32"), 3)
             other = "bf16" if args.prec == "fp16" else "fp16"
             extras[f"svd_{other}_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", other), 5)

@@ -261,7 +261,7 @@ int sp_set_wait_budget(long long iterations);
  * of frames): n independent streams, each with its own basis (array, grid, N, K), frames
  * and frame count, localised by one CUDA-graph launch whose branches run concurrently.
  * Each stream computes exactly what sp_localize computes for it (same kernels, same
- * results); where a basis has no tensor-core path (2K > 256 or M > 16) an FP16/BF16 request
+ * results); where a basis has no tensor-core path (2K > 320 or M > 16) an FP16/BF16 request
  * runs that stream in FP32.
  *
  * sp_batch_create: bases[i] (must outlive the plan), frames_dev[i] (device [T[i]][M][B]
@@ -309,9 +309,9 @@ int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *
 
 /* Create a proposal for basis b (which must outlive it): C cell directions cell_dirs
  * [C][3] (host, need not be unit length), hidden sizes H1, H2 (multiples of 64 in
- * [64, 256]), 1 <= C <= 4096, 2K <= 256.  Weights are drawn uniformly in
+ * [64, 256]), 1 <= C <= 4096, 2K <= 320.  Weights are drawn uniformly in
  * +-sqrt(6 / fan_in) from a counter-based generator keyed by seed; biases are 0.
- * Synchronous.  Errors: SP_EINVAL (bad arguments), SP_ENOTIMPL (2K > 256). */
+ * Synchronous.  Errors: SP_EINVAL (bad arguments), SP_ENOTIMPL (2K > 320). */
 int sp_proposal_create(const sp_basis *b, const double *cell_dirs, int C, int H1, int H2,
                        unsigned long long seed, sp_proposal **out);
 void sp_proposal_destroy(sp_proposal *p);

@@ -76,6 +76,7 @@ struct TcLayout {
     int k2 = 0;                   // GEMM2 K = 2K rounded up to 16
     int k2_atoms = 0;             // 64-element atoms of the GEMM2 K dimension
     int n2 = 128;                 // Q tile of GEMM2
+    int v_box = 0;                // rows per TMA box of a V atom (n1, or n1 / 2 when n1 > 256)
 };
 TcLayout make_tc_layout(int P, int B, int K);
 

@@ -41,7 +41,8 @@ constexpr int kWRing = 4;             // weight atoms in flight
 constexpr int kWAtomBytes = 256 * 128;
 constexpr int kAAtomBytes = 128 * 128;
 constexpr int kTop = 8;               // cells tracked per frame
-constexpr int kMaxF = 256, kMaxH = 256, kMaxC = 4096;
+constexpr int kMaxF = 320, kMaxH = 256, kMaxC = 4096;
+constexpr int kAAtoms = kMaxF / 64;   // A buffer: features (up to 5 atoms) or a hidden layer (4)
 constexpr double kCellTie = 1e-12;
 constexpr long long kDrain = 4000000000LL;
 
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int off_w = 4 * kAAtomBytes;
+    const int off_w = kAAtoms * kAAtomBytes;
     const int off_bias = off_w + kWRing * kWAtomBytes;
     const int n_bias = prm.H1 + prm.H2 + prm.C;
     const int off_bar = off_bias + ((n_bias * 4 + 15) / 16) * 16;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                 const int F2 = prm.F_atoms * 32;
                 const long long base = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
                 for (int r0 = 0; r0 < 32; r0 += 4) {
-                    float2 zv[4][4];
+                    float2 zv[4][kAAtoms];
                     float inv[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                         const float n2 = lv ? prm.zn2[fr] : 0.f;
                         inv[u] = n2 > 0.f ? rsqrtf(n2) : 0.f;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
+                        for (int i = 0; i < kAAtoms; ++i) {
                             const int k = lane + 32 * i;
                             zv[u][i] = (lv && k < prm.K) ? __ldg(prm.Z + (size_t)fr * prm.K + k) : make_float2(0.f, 0.f);
                         }
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     for (int u = 0; u < 4; ++u) {
                         const int row = warp * 32 + r0 + u;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
+                        for (int i = 0; i < kAAtoms; ++i) {
                             const int k = lane + 32 * i;
                             if (k < F2) {
                                 const int n = 2 * k;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 // in FP32 and the best of those is the frame's direction: the result equals an FP32 search
 // over all the candidates.
 constexpr int kMaxRounds = 16;    // <= 512 candidates per frame
-constexpr int kMaxKp = 128;       // K <= 128
+constexpr int kMaxKp = 160;       // K <= 160
 
 struct RescoreParams {
     const int32_t *top;
@@ -563,7 +564,7 @@ __device__ __forceinline__ unsigned long long pack_key(float v, int q) {
 }
 
 __global__ void __launch_bounds__(256) fallback_scan_kernel(const FallbackParams prm) {
-    __shared__ float2 zs[kFbFrames][128];
+    __shared__ float2 zs[kFbFrames][kMaxKp];
     const int n = *prm.count, K = prm.K;
     const int n_groups = (n + kFbFrames - 1) / kFbFrames, n_slices = (prm.Qr + kFbClasses - 1) / kFbClasses;
     const int lane = threadIdx.x & 31;
@@ -949,8 +950,8 @@ int launch_mlp(const sp_proposal *p, const void *Z, const float *zn2, int T, flo
     SP_TRY(device_status_ptr(&m.status));
     m.budget = wait_budget();
     const int n_bias = p->H1 + p->H2 + p->C;
-    const int smem = 4 * kAAtomBytes + kWRing * kWAtomBytes + ((n_bias * 4 + 15) / 16) * 16 + (2 * kWRing + 6) * 8 +
-                     16 + 1024;
+    const int smem = kAAtoms * kAAtomBytes + kWRing * kWAtomBytes + ((n_bias * 4 + 15) / 16) * 16 +
+                     (2 * kWRing + 6) * 8 + 16 + 1024;
     static bool attr = false;
     if (!attr) {
         SP_CUDA(cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
@@ -975,7 +976,7 @@ int sp_proposal_create(const sp_basis *b, const double *cell_dirs, int C, int H1
     SP_CHECK(C >= 1 && C <= kMaxC, SP_EINVAL, "sp_proposal_create: C must be in [1, 4096]");
     SP_CHECK(H1 >= 64 && H1 <= kMaxH && H1 % 64 == 0 && H2 >= 64 && H2 <= kMaxH && H2 % 64 == 0, SP_EINVAL,
              "sp_proposal_create: hidden sizes must be multiples of 64 in [64, 256]");
-    SP_CHECK(2 * b->K <= kMaxF && b->K <= kMaxKp, SP_ENOTIMPL, "sp_proposal_create: 2K must be <= 256");
+    SP_CHECK(2 * b->K <= kMaxF && b->K <= kMaxKp, SP_ENOTIMPL, "sp_proposal_create: 2K must be <= 320");
     for (int c = 0; c < C; ++c) {
         const double *d = cell_dirs + 3 * c;
         SP_CHECK(std::isfinite(d[0]) && std::isfinite(d[1]) && std::isfinite(d[2]) &&

@@ -80,7 +80,7 @@ constexpr int kGroupPairs = 24;       // pairs per stage group (3 atoms)
 constexpr int kAtomElems = 64;        // 16-bit elements per swizzle atom row
 constexpr int kAtomBytes = 128 * 128; // one 128-row atom
 constexpr int kGroupElems = 3 * kAtomElems;
-constexpr int kMaxN1 = 256;           // GEMM1 N limit (UMMA N <= 256)
+constexpr int kMaxN1 = 320;           // GEMM1 N limit (two MMAs of N <= 256 above 256)
 constexpr int kMaxN1Smem = 144;       // widest basis of the shared-memory A plan
 constexpr int kProdWarps = 16;
 constexpr int kProjThreads = 22 * 32; // 16 producer, 4 epilogue, 1 TMA, 1 MMA warps
@@ -89,7 +89,7 @@ constexpr int kZBuf = 256;            // TMEM column offset of the second Z buff
 constexpr int kScanThreads = 256;     // 4 epilogue, 1 TMA, 1 MMA, 2 helper warps
 constexpr int kN2 = 64;               // direction classes per GEMM2 tile
 constexpr int kCap = 16;              // candidates kept per frame
-constexpr int kRing = 4;              // GEMM2 D-tile / TMEM buffers in flight
+constexpr int kRingMax = 4;           // GEMM2 D-tile / TMEM buffers in flight (2 when 2K > 256)
 
 TcLayout make_tc_layout(int P, int B, int K) {
     TcLayout t;
@@ -150,6 +150,7 @@ struct ProjParams {
     int T, M, B, P, G, n_chunks;
     int n1, K, n_tiles;
     int n_zbuf, z_cols, a_col0, n_aslot, n_vslot;   // tensor-memory plan of svd_proj_tm_kernel
+    int v_box;                                      // rows per TMA box of a V atom
     float inv_vscale;
     float2 *z_out;       // [T][K] complex64
     float *zn2_out;      // [T] ||Z||^2 or null
@@ -268,6 +269,12 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                 uint32_t ad[8];
 #pragma unroll
                 for (int x = 0; x < 8; ++x) ad[x] = A + sw[x];
+                // address of local pair pl: a table lookup when pl is known at compile time,
+                // else the swizzle arithmetic (a runtime index would put ad[] in local memory)
+                auto pair_addr = [&](int pl) -> uint32_t {
+                    return (EXACT ? ad[pl & 7] : A + (uint32_t)(f * 128 + b * 4 + (((pl & 7) ^ (f & 7)) << 4))) +
+                           (uint32_t)((pl >> 3) * kAtomBytes);
+                };
                 const int p_lo = g * kGroupPairs;
                 const int npg = min(kGroupPairs, P - p_lo);
 #pragma unroll
@@ -279,14 +286,12 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                         if (pl >= 0 && pl < npg) {
                             const float2 a0 = xh[i], b0 = xh[jj];
                             const uint32_t w = pack2<BF16>(a0.x * b0.x + a0.y * b0.y, a0.y * b0.x - a0.x * b0.y);
-                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(ad[pl & 7] + (pl >> 3) * kAtomBytes), "r"(w)
-                                         : "memory");
+                            asm volatile("st.shared.b32 [%0], %1;" ::"r"(pair_addr(pl)), "r"(w) : "memory");
                         }
                     }
                 }
                 if (npg & 1)  // zero partner slot of an odd last pair
-                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(ad[npg & 7] + (npg >> 3) * kAtomBytes), "r"(0u)
-                                 : "memory");
+                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(pair_addr(npg)), "r"(0u) : "memory");
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&full_a[s]);
@@ -314,12 +319,13 @@ __global__ void __launch_bounds__(kProjThreads, 1)
             }
             ptx::tc_fence_after();
             const long long frame = (long long)((int)blockIdx.x + li * (int)gridDim.x) * 128 + r;
-            float2 *zo = prm.z_out + (size_t)(frame < prm.T ? frame : 0) * prm.K;
+            const bool live = frame < prm.T;
+            float2 *zo = prm.z_out + (size_t)(live ? frame : 0) * prm.K;
             float zn2 = 0.f;
             for (int c0 = 0; c0 < n1; c0 += 32) {
                 float v[32];
                 ptx::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(zb * kZBuf + c0), v);
-                if (frame < prm.T) {
+                if (live) {
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) {
                         const int kk = (c0 + i) >> 1;
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                     }
                 }
             }
-            if (prm.zn2_out && frame < prm.T) prm.zn2_out[frame] = zn2;
+            if (prm.zn2_out && live) prm.zn2_out[frame] = zn2;
             ptx::tc_fence_before();
             ptx::mbar_arrive(&zempty[zb]);
         }
@@ -587,12 +593,13 @@ __global__ void __launch_bounds__(kProjThreads, 1)
             }
             ptx::tc_fence_after();
             const long long frame = (long long)((int)blockIdx.x + li * (int)gridDim.x) * 128 + r;
-            float2 *zo = prm.z_out + (size_t)(frame < prm.T ? frame : 0) * prm.K;
+            const bool live = frame < prm.T;
+            float2 *zo = prm.z_out + (size_t)(live ? frame : 0) * prm.K;
             float zn2 = 0.f;
             for (int c0 = 0; c0 < n1; c0 += 32) {
                 float v[32];
                 ptx::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(zb * prm.z_cols + c0), v);
-                if (frame < prm.T) {
+                if (live) {
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) {
                         const int kk = (c0 + i) >> 1;
@@ -604,7 +611,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                     }
                 }
             }
-            if (prm.zn2_out && frame < prm.T) prm.zn2_out[frame] = zn2;
+            if (prm.zn2_out && live) prm.zn2_out[frame] = zn2;
             ptx::tc_fence_before();
             ptx::mbar_arrive(&zempty[zb]);
         }
@@ -623,10 +630,13 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                 const int g = sl % prm.G;
                 const int npg = min(kGroupPairs, prm.P - g * kGroupPairs);
                 const int atoms = (((npg + 1) >> 1) + 3) >> 2;
+                const int vcol = sl * kGroupElems;
                 ptx::mbar_arrive_expect_tx(&full_v[s], (uint32_t)(atoms * n1 * 128));
                 uint8_t *Bs = smem + s * b_stage;
                 for (int a = 0; a < atoms; ++a)
-                    ptx::tma_load_2d(Bs + a * n1 * 128, &tmap_v, &full_v[s], sl * kGroupElems + a * kAtomElems, 0);
+                    for (int r0 = 0; r0 < n1; r0 += prm.v_box)   // a box spans at most 256 rows
+                        ptx::tma_load_2d(Bs + a * n1 * 128 + r0 * 128, &tmap_v, &full_v[s], vcol + a * kAtomElems,
+                                         r0);
                 issued = st;
             }
             for (int st = max(0, issued - n_vs + 1); st <= issued; ++st)
@@ -635,7 +645,10 @@ __global__ void __launch_bounds__(kProjThreads, 1)
         __syncwarp();
     } else {  // kMmaWarp
         if (lane == 0) {
-            const uint32_t idesc = ptx::idesc_f16(128, n1, BF16);
+            // GEMM1 N above 256 runs as two MMAs per K step: columns [0, 256) and [256, n1)
+            const int nA = n1 <= 256 ? n1 : 256, nB = n1 - nA;
+            const uint32_t idesc = ptx::idesc_f16(128, nA, BF16);
+            const uint32_t idesc_b = ptx::idesc_f16(128, nB > 0 ? nB : 16, BF16);
             int st = 0;
             for (int li = 0; li < my_tiles; ++li) {
                 const int zb = n_zb == 2 ? (li & 1) : 0;
@@ -666,6 +679,10 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                         const uint32_t bo = (k >> 2) * n1 * 128 + (k & 3) * 32;
                         ptx::mma_f16_ts(d_tmem, a_tmem + (uint32_t)(k * 8), ptx::sw128_desc(b_base + bo), idesc,
                                         (sl > 0 || k > 0) ? 1u : 0u);
+                        if (nB > 0)
+                            ptx::mma_f16_ts(d_tmem + (uint32_t)nA, a_tmem + (uint32_t)(k * 8),
+                                            ptx::sw128_desc(b_base + bo + (uint32_t)nA * 128u), idesc_b,
+                                            (sl > 0 || k > 0) ? 1u : 0u);
                     }
                     ptx::mma_commit(&empty_a[sa]);
                     ptx::mma_commit(&empty_v[sv]);
@@ -700,7 +717,7 @@ struct ScanParams {
     float *proj;
 };
 
-template <int BF16>
+template <int BF16, int kRing>
 __global__ void __launch_bounds__(kScanThreads, 2)
     svd_scan_kernel(const __grid_constant__ CUtensorMap tmap_d, const ScanParams prm) {
     extern __shared__ uint8_t smem_raw[];
@@ -967,6 +984,7 @@ int tc_prepare(sp_basis *b) {
     const sp_steering *st = b->st;
     const int K = b->K, P = st->P, B = st->B, L = st->L;
     TcLayout t = make_tc_layout(P, B, K);
+    t.v_box = t.n1 <= 256 ? t.n1 : t.n1 / 2;   // a TMA box spans at most 256 rows
     b->tc = t;
     if (t.n1 > kMaxN1 || st->M > 16) {
         b->tc.n1 = 0;  // tensor-core path unavailable for this basis
@@ -1021,7 +1039,7 @@ int tc_prepare(sp_basis *b) {
         SP_TRY(b->Dtc[prec].reserve(hd.size() * 2));
         SP_CUDA(cudaMemcpy(b->Vtc[prec].p, hv.data(), nv * 2, cudaMemcpyHostToDevice));
         SP_CUDA(cudaMemcpy(b->Dtc[prec].p, hd.data(), hd.size() * 2, cudaMemcpyHostToDevice));
-        int rc = encode_tmap_2d(&maps->v[prec], b->Vtc[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.n1);
+        int rc = encode_tmap_2d(&maps->v[prec], b->Vtc[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.v_box);
         if (rc == SP_OK) rc = encode_tmap_2d(&maps->d[prec], b->Dtc[prec].p, prec, dcols, Qr, kAtomElems, kN2);
         if (rc != SP_OK) {
             delete maps;
@@ -1053,7 +1071,7 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "tensor-core path supports 2K <= 256 and M <= 16 (use SP_PREC_FP32)");
+             "tensor-core path supports 2K <= 320 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
     ProjParams p;
@@ -1066,10 +1084,10 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     p.n_chunks = t.n_chunks;
     p.n1 = t.n1;
     p.K = b->K;
-    p.n_tiles = (int)(((long long)T + 127) / 128);
     p.inv_vscale = 1.f / b->v_scale;
     p.z_out = (float2 *)z_out;
     p.zn2_out = zn2_out;
+    p.n_tiles = (int)(((long long)T + 127) / 128);
     const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
     // variants: exactly 7 microphones (the Table 2 arrays), up to 8, up to 16
     const int which = bf * 3 + (p.M == 7 ? 0 : p.M <= 8 ? 1 : 2);
@@ -1096,7 +1114,8 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
         p.a_col0 = p.z_cols;
         p.n_aslot = std::min(kMaxASlots, (512 - p.a_col0) / kAStageCols);
         const int b_stage = 3 * t.n1 * 128;
-        p.n_vslot = std::min(kMaxVSlots, (200 * 1024) / b_stage);
+        p.n_vslot = std::min(kMaxVSlots, (216 * 1024) / b_stage);
+        p.v_box = t.v_box;
         SP_CHECK(p.n_aslot >= 2 && p.n_vslot >= 2, SP_ENOTIMPL, "tensor-core plan: too few pipeline stages");
         const int smem = p.n_vslot * b_stage + 256 + 1024;
         SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
@@ -1121,7 +1140,7 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "tensor-core path supports 2K <= 256 and M <= 16 (use SP_PREC_FP32)");
+             "tensor-core path supports 2K <= 320 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
     ScanParams p;
@@ -1141,13 +1160,19 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     p.tol_abs = (float)(2.0 * 1e-6 * L);
     p.idx = idx;
     p.proj = proj;
-    const int smem = t.k2_atoms * kAtomBytes + kRing * t.k2_atoms * kN2 * 128 + 128 * kCap * 4 + 128 * 4 +
-                     (4 * kRing + 3) * 8 + 1024;
-    auto kern = bf ? svd_scan_kernel<1> : svd_scan_kernel<0>;
-    static bool attr[2] = {false, false};
-    if (!attr[bf]) {
+    // four D tiles in flight, two when the Z tile and four D tiles would not fit (2K > 256)
+    const int ring = 3 * t.k2_atoms * kAtomBytes + 128 * kCap * 4 <= 216 * 1024 ? kRingMax : 2;
+    const int smem = t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 128 * kCap * 4 + 128 * 4 +
+                     (4 * ring + 3) * 8 + 1024;
+    SP_CHECK(smem <= 232448, SP_ENOTIMPL, "scan: shared-memory plan exceeds 227 KB");
+    const int which = bf * 2 + (ring == kRingMax ? 0 : 1);
+    void (*const kerns[4])(CUtensorMap, ScanParams) = {svd_scan_kernel<0, kRingMax>, svd_scan_kernel<0, 2>,
+                                                       svd_scan_kernel<1, kRingMax>, svd_scan_kernel<1, 2>};
+    auto kern = kerns[which];
+    static bool attr[4] = {false, false, false, false};
+    if (!attr[which]) {
         SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-        attr[bf] = true;
+        attr[which] = true;
     }
     const unsigned grid = (unsigned)(((long long)T + 127) / 128);
     kern<<<grid, kScanThreads, smem, s>>>(maps->d[bf], p);

@@ -278,6 +278,13 @@ def workload(name: str, T: int | None = None, seed_offset: int = 0):
         src = random_directions(rng, T)[:, None, :]
         snr = rng.uniform(-5.0, 20.0, size=T)
         frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "white")
+    elif name == "ball16_n1024_q642":   # 16 mics in a 5 cm-radius ball, N=1024, Q=642: 2K > 256
+        rng = np.random.default_rng([SEED_BASE + 7, 4])
+        mic, lvl, N = array_random_ball(rng, 16), 3, 1024
+        T = 200 if T is None else T
+        src = random_directions(rng, T)[:, None, :]
+        snr = rng.uniform(-5.0, 20.0, size=T)
+        frames = plane_wave_frames(rng, mic, T, N, fs, c, src, snr, "white")
     else:
         raise ValueError(f"unknown workload {name}")
     return dict(name=name, mic_xyz=mic, dirs=icosphere(lvl), fs=fs, c=c, N=N, delta=1e-5,

@@ -43,7 +43,7 @@ def test_batch_equals_per_stream_localize(prec, autotune):
     if autotune:
         assert info["ms"] > 0
     for i, (b, f) in enumerate(zip(bases, frames)):
-        ref_prec = "fp32" if 2 * b.K > 256 or b.steering.M > 16 else prec   # no tensor-core plan
+        ref_prec = "fp32" if 2 * b.K > 320 or b.steering.M > 16 else prec   # no tensor-core plan
         idx, score, proj = sp.localize(b, f, "svd_exhaustive", ref_prec)
         assert torch.equal(bt.idx[i], idx), i
         assert torch.equal(bt.proj[i], proj), i
@@ -54,7 +54,7 @@ def test_localize_batched_matches_and_agrees_with_oracle():
     wls, bases, frames = _streams()
     idx, score, proj = sp.localize_batched(bases, frames, "svd_exhaustive", "fp16")
     for i in range(len(bases)):
-        ref_prec = "fp32" if 2 * bases[i].K > 256 else "fp16"
+        ref_prec = "fp32" if 2 * bases[i].K > 320 else "fp16"
         ref = sp.localize(bases[i], frames[i], "svd_exhaustive", ref_prec)
         assert torch.equal(idx[i], ref[0]) and torch.equal(proj[i], ref[2])
     Ms = [wl["mic_xyz"].shape[0] for wl in wls]
@@ -72,11 +72,11 @@ def test_localize_batched_matches_and_agrees_with_oracle():
 
 
 def test_batch_mixes_tensor_core_and_fp32_streams():
-    """A basis beyond the tensor-core plan (2K > 256) runs its stream in FP32 inside the same
+    """A basis beyond the tensor-core plan (2K > 320) runs its stream in FP32 inside the same
     launch, with the same result as sp_localize in FP32."""
     wls, bases, frames = _streams()
-    big = [i for i, b in enumerate(bases) if 2 * b.K > 256]
-    small = [i for i, b in enumerate(bases) if 2 * b.K <= 256]
+    big = [i for i, b in enumerate(bases) if 2 * b.K > 320]
+    small = [i for i, b in enumerate(bases) if 2 * b.K <= 320]
     if not big or not small:
         pytest.skip("the seeded streams hold no mix of large and small ranks")
     sel = big[:2] + small[:2]
@@ -93,7 +93,7 @@ def test_batch_mixes_tensor_core_and_fp32_streams():
 @pytest.mark.parametrize("mode,prec", [("svd_kdtree", "fp16"), ("svd_exhaustive", "bf16")])
 def test_batch_other_modes_equal_per_stream(mode, prec):
     wls, bases, frames = _streams()
-    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 256][:6]
+    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 320][:6]
     bt = sp.Batch([bases[i] for i in sel], [frames[i] for i in sel], mode, prec)
     bt.run()
     torch.cuda.synchronize()

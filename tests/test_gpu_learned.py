@@ -267,3 +267,29 @@ def test_bf16_learned_fallback_equals_exhaustive():
     torch.cuda.synchronize()
     assert bool(fb.all())
     assert torch.equal(li, ei) and torch.equal(ls, es)
+
+
+def test_wide_basis_inference_and_search():
+    """2K = 262 features (five 64-column atoms) on the 16-mic N = 1024 array: tensor-core
+    logits against the FP64 forward, and the search with every frame falling back equals the
+    exhaustive result."""
+    d = _setup("ball16_n1024_q642", 200)
+    b = oracle_basis_in_library(d)
+    cells = I.icosphere(1)
+    p = sp.Proposal(b, cells, hidden=(128, 128), seed=1)
+    assert p.F == 2 * d["ob"]["K"] and p.F > 256
+    theta = _params(p, 51)
+    theta[-(p.H2 * p.C + p.C):] *= 8.0
+    p.set_params(theta)
+    Z64 = d["Z"].astype(np.complex64)
+    Zt = torch.from_numpy(Z64).cuda()
+    zn2 = torch.from_numpy(np.sum(np.abs(Z64.astype(np.complex128)) ** 2, axis=1).astype(np.float32)).cuda()
+    top, conf, lg = p.infer(Zt, zn2, logits=True)
+    torch.cuda.synchronize()
+    sp.check_status()
+    ref = _oracle_logits(p, theta, Z64)
+    assert np.max(np.abs(lg.cpu().numpy() - ref) / (1 + np.abs(ref))) <= 5e-3
+    li, _, _, fb = p.localize(d["frames"], "fp16", n_top=4, theta=2.0)
+    ei, _, _ = sp.localize(b, d["frames"], "svd_exhaustive", "fp16")
+    torch.cuda.synchronize()
+    assert bool(fb.all()) and torch.equal(li, ei)
