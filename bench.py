@@ -40,10 +40,10 @@ UNIT = "frames/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes read + written per frame by svd_proj_kernel, from one ncu capture of this
-# version of the kernel on 19,456 frames of the same workload (311.3 MB / 19,456), scaled to
+# version of the kernel on 19,456 frames of the same workload (311.0 MB / 19,456), scaled to
 # a launch by the frame count (traffic grows in proportion to frames).  Set to None when the
 # kernel changes until it is captured again.
-TRAFFIC_PER_FRAME = 16001.0
+TRAFFIC_PER_FRAME = 15985.0
 
 
 def _peaks():
@@ -501,7 +501,7 @@ def main():
                          "frac": achieved / peak, "traffic": TRAFFIC_PER_FRAME and TRAFFIC_PER_FRAME * T,
                          "kernel": "svd_proj_kernel", "kernel_ms": k_ms, "peak_source": peak_kind,
                          "algorithmic_bytes_per_frame": per_frame_bytes},
-            "kernel_ms": {"svd_proj_kernel": k_ms, "svd_scan_kernel": scan_ms, "score_row_kernel": step4_ms},
+            "kernel_ms": {"svd_proj_kernel": k_ms, "svd_scan_kernel": scan_ms, "step4_bulk_kernel": step4_ms},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                              "sample": "2048 frames of the same workload (PHAT, Z = V^H X, Re{D Z} argmax, "
                                        "online step 4 in FP64 numpy)"},

@@ -2,14 +2,19 @@
 //
 // Same arithmetic as score_row_kernel (simt.cu): because tau_{q,i,j} = d_j - d_i with
 // d_m = fs/c r_m . u_q, W_ij X_ij = y_i conj(y_j) with y_m[k] = x^_m[k] exp(-2 pi i k d_m / N),
-// and sum_{i<j} Re{y_i conj(y_j)} = (|sum_m y_m|^2 - sum_m |y_m|^2) / 2 per bin.
+// and sum_{i<j} Re{y_i conj(y_j)} = (|sum_m y_m|^2 - sum_m |y_m|^2) / 2 per bin.  |y_m|^2 is
+// 1 for every microphone whose PHAT is defined and 0 for the others (Eq. 3 zero rule), so the
+// second sum is a count: Y = (sum_k |sum_m y_m[k]|^2 - n_valid) / 2.
 //
 // Layout of the work: frames are taken in pairs (2 M B complex64 = 16 M B bytes, so every
 // pair starts 16-byte aligned when the batch does); one CTA per SM walks its pairs through a
-// ring of 4 shared-memory slots filled by one producer thread with cp.async.bulk, while 16
-// consumer warps compute (4 per slot: frame 0 or 1 of the pair x even or odd 32-bin half).
-// The odd last frame of an odd batch is read from global memory by its warps.  Every wait is
-// bounded; a wait that gives up records status bit 4 and the CTA drains and returns.
+// ring of up to 8 shared-memory slots filled by one producer thread with cp.async.bulk, while
+// 16 consumer warps compute in 4 teams (a team's 4 warps: frame 0 or 1 of the pair x even or
+// odd 32-bin half).  Local pair j lands in slot j mod n_slots and is taken by team j mod 4,
+// so with more slots than teams every team finds its next pair already loaded while the
+// other slots stay in flight.  The odd last frame of an odd batch is read from global memory
+// by its warps.  Every wait is bounded; a wait that gives up records status bit 4 and the CTA
+// drains and returns.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -19,15 +24,16 @@
 namespace sp {
 namespace {
 
-constexpr int kSlots = 4;
-constexpr int kConsumerWarps = 16;
+constexpr int kMaxSlots = 8;
+constexpr int kTeams = 4;
+constexpr int kConsumerWarps = 4 * kTeams;
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
 constexpr float kZero2 = 1e-30f;
 constexpr long long kDrainCycles = 4000000000LL;
 
 struct Step4Params {
     const float2 *frames;
-    int T, M, B, n_pairs;
+    int T, M, B, n_pairs, n_slots;
     unsigned pair_bytes;   // 16 M B
     const float4 *tab;     // [Q][M]: d_m / N as float hi + lo, 64-bin step phasor (cos, sin)
     const int32_t *idx;
@@ -44,13 +50,14 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
     const int B = prm.B;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned slot_bytes = (prm.pair_bytes + 127) / 128 * 128;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSlots * slot_bytes);
-    uint64_t *empty = full + kSlots;
-    float *part = reinterpret_cast<float *>(empty + kSlots);          // [slot][frame]
-    volatile int *dec = reinterpret_cast<volatile int *>(part + 2 * kSlots);   // [slot][frame]
-    volatile int *abort_flag = dec + 2 * kSlots;
+    const int n_slots = prm.n_slots;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + n_slots * slot_bytes);
+    uint64_t *empty = full + kMaxSlots;
+    float *part = reinterpret_cast<float *>(empty + kMaxSlots);          // [team][frame]
+    volatile int *dec = reinterpret_cast<volatile int *>(part + 2 * kTeams);   // [team][frame]
+    volatile int *abort_flag = dec + 2 * kTeams;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kSlots; ++s) {
+        for (int s = 0; s < n_slots; ++s) {
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 4);
         }
@@ -66,9 +73,9 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
         if (lane == 0) {
             int issued = -1;
             for (int i = 0; i < my_pairs; ++i) {
-                const int s = i % kSlots;
+                const int s = i % n_slots;
                 if (*abort_flag) break;
-                if (!ptx::mbar_wait(&empty[s], ((i / kSlots) & 1) ^ 1, budget)) {
+                if (!ptx::mbar_wait(&empty[s], ((i / n_slots) & 1) ^ 1, budget)) {
                     *abort_flag = 1;
                     atomicOr(prm.status, 4);
                     break;
@@ -85,32 +92,34 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
                 }
                 issued = i;
             }
-            for (int i = issued - kSlots + 1; i <= issued; ++i)
-                if (i >= 0) ptx::mbar_wait(&full[i % kSlots], (i / kSlots) & 1, kDrainCycles);
+            for (int i = issued - n_slots + 1; i <= issued; ++i)
+                if (i >= 0) ptx::mbar_wait(&full[i % n_slots], (i / n_slots) & 1, kDrainCycles);
         }
         __syncwarp();
         return;
     }
 
-    // ---------------- consumers: warp = (slot, frame h of the pair, bin half g)
-    const int s = warp >> 2, h = (warp >> 1) & 1, gh = warp & 1;
-    const float2 *smem_frame = reinterpret_cast<const float2 *>(smem + s * slot_bytes) + (size_t)h * M * B;
-    const int bar_id = 1 + s * 2 + h;   // the two bin halves of frame h (64 threads)
-    for (int i = s; i < my_pairs; i += kSlots) {
+    // ---------------- consumers: warp = (team, frame h of the pair, bin half g)
+    const int team = warp >> 2, h = (warp >> 1) & 1, gh = warp & 1;
+    const int bar_id = 1 + team * 2 + h;   // the two bin halves of frame h (64 threads)
+    for (int i = team; i < my_pairs; i += kTeams) {
+        const int s = i % n_slots;
+        const float2 *smem_frame = reinterpret_cast<const float2 *>(smem + s * slot_bytes) + (size_t)h * M * B;
         // Both warps of a frame leave the loop together: the g = 0 warp reads the abort flag
         // before the barrier and both act on that one reading after it.
-        const bool ok = ptx::mbar_wait_warp(&full[s], (i / kSlots) & 1, budget);
+        const bool ok = ptx::mbar_wait_warp(&full[s], (i / n_slots) & 1, budget);
         if (!ok && lane == 0) {
             *abort_flag = 1;
             atomicOr(prm.status, 4);
         }
-        if (gh == 0 && lane == 0) dec[s * 2 + h] = *abort_flag;
+        if (gh == 0 && lane == 0) dec[team * 2 + h] = *abort_flag;
         ptx::named_bar_sync(bar_id, 64);
-        if (dec[s * 2 + h]) break;
+        if (dec[team * 2 + h]) break;
         const long long pair = (long long)blockIdx.x + (long long)i * gridDim.x;
         const long long t = 2 * pair + h;
         const bool whole = 2 * pair + 1 < prm.T;
         float acc = 0.f;
+        int n_valid = 0;
         int q = -1;
         if (t < prm.T) q = prm.idx[t];
         if (q >= 0) {
@@ -142,33 +151,34 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
                 }
             }
             for (int k = k_first; k < B; k += 64) {
-                float sr = 0.f, si = 0.f, en = 0.f;
+                float sr = 0.f, si = 0.f;
 #pragma unroll
                 for (int m = 0; m < MMAX; ++m) {
                     if (m < M) {
                         const float2 x = fr[(size_t)m * B + k];
                         const float mag2 = x.x * x.x + x.y * x.y;
                         const float2 w = ph[m];
-                        const float r = mag2 >= kZero2 ? rsqrtf(mag2) : 0.f;
+                        const bool valid = mag2 >= kZero2;
+                        const float r = valid ? rsqrtf(mag2) : 0.f;
+                        n_valid += valid ? 1 : 0;
                         const float xr = x.x * r, xi = x.y * r;
-                        const float yr = xr * w.x - xi * w.y, yi = xr * w.y + xi * w.x;
-                        sr += yr;
-                        si += yi;
-                        en += yr * yr + yi * yi;
+                        sr += xr * w.x - xi * w.y;
+                        si += xr * w.y + xi * w.x;
                         const float2 st = stp[m];
                         ph[m] = make_float2(w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x);
                     }
                 }
-                acc += 0.5f * (sr * sr + si * si - en);
+                acc = fmaf(sr, sr, fmaf(si, si, acc));
             }
+            acc = 0.5f * (acc - (float)n_valid);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         }
         // the two bin halves of frame h meet at their named barrier
-        if (gh == 1 && lane == 0) part[s * 2 + h] = acc;
+        if (gh == 1 && lane == 0) part[team * 2 + h] = acc;
         ptx::named_bar_sync(bar_id, 64);
         if (gh == 0 && lane == 0 && t < prm.T)
-            prm.score[t] = q < 0 ? __int_as_float(0x7fc00000) : acc + part[s * 2 + h];
+            prm.score[t] = q < 0 ? __int_as_float(0x7fc00000) : acc + part[team * 2 + h];
         ptx::named_bar_sync(bar_id, 64);   // part[] and dec[] are reused by the next pair
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&empty[s]);
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
 }  // namespace
 
 // Returns SP_ENOTIMPL when the bulk-copy plan does not apply (unaligned batch, M > 16, or a
-// frame pair larger than a quarter of the shared memory); the caller then uses
+// frame pair above 48 KB, which leaves fewer than four slots); the caller then uses
 // score_row_kernel.
 int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const int32_t *idx, float *score,
                       cudaStream_t s) {
@@ -193,13 +203,14 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
     p.B = st->B;
     p.n_pairs = (T + 1) / 2;
     p.pair_bytes = pair_bytes;
+    const unsigned slot_bytes = (pair_bytes + 127) / 128 * 128;
+    p.n_slots = (int)std::min<unsigned>(kMaxSlots, (200u * 1024u) / slot_bytes);   // 7 for M = 7, N = 512
     p.tab = st->step4_tab.as<float4>();
     p.idx = idx;
     p.score = score;
     SP_TRY(device_status_ptr(&p.status));
     p.budget = wait_budget();
-    const unsigned slot_bytes = (pair_bytes + 127) / 128 * 128;
-    const int smem = (int)(kSlots * slot_bytes + 2 * kSlots * 8 + 4 * kSlots * 4 + 16 + 128);
+    const int smem = (int)(p.n_slots * slot_bytes + 2 * kMaxSlots * 8 + 4 * kTeams * 4 + 16 + 128);
     auto kern = st->M == 7 ? step4_bulk_kernel<7, true>
                            : st->M <= 8 ? step4_bulk_kernel<8, false> : step4_bulk_kernel<16, false>;
     const int which = st->M == 7 ? 0 : st->M <= 8 ? 1 : 2;
