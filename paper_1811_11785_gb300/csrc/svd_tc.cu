@@ -883,12 +883,14 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     }
     __syncthreads();
 
-    // -------- rescoring in FP32: a warp takes two frames at a time (16 lanes each); lane
-    // (c, part) sums the terms k = part, part + 4, ... of candidate c, 4 candidates per round.
+    // -------- rescoring in FP32: a warp takes four frames at a time (8 lanes each); lane
+    // (c, part) sums the terms k = part, part + 4, ... of candidate c, 2 candidates per round
+    // (frames carry 1-2 candidates on typical inputs).  The terms of a 64-term block are
+    // loaded in one unrolled batch, so a round costs one L2 round trip after the class lookup.
     if (!*abort_flag) {
-        const int h = lane >> 4, c4 = (lane >> 2) & 3, part = lane & 3;
-        for (int r0 = 2 * warp; r0 < 128; r0 += 2 * (kScanThreads / 32)) {
-            const int r = r0 + h;
+        const int g4 = lane >> 3, c2 = (lane >> 2) & 1, part = lane & 3;
+        for (int r0 = 4 * warp; r0 < 128; r0 += 4 * (kScanThreads / 32)) {
+            const int r = r0 + g4;
             const long long frame = t0 + r;
             const bool live = frame < T;
             const int n = live ? cnt_s[r] : 0;
@@ -896,19 +898,30 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             const float2 *zr = prm.Z + (size_t)(live ? frame : 0) * K;
             float best = 0.f;
             int bq = -1;
-            const int tmax = max(total, __shfl_xor_sync(0xffffffffu, total, 16));
-            for (int base = 0; base < tmax; base += 4) {
-                const int c = base + c4;
+            int tmax = max(total, __shfl_xor_sync(0xffffffffu, total, 8));
+            tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, 16));
+            for (int base = 0; base < tmax; base += 2) {
+                const int c = base + c2;
                 int q = -1;
-                if (c < total) q = prm.reps[n <= kCap ? cand[r * kCap + c] : c];
+                if (c < total) q = __ldg(prm.reps + (n <= kCap ? cand[r * kCap + c] : c));
                 float acc = 0.f;
                 if (q >= 0) {
                     const float2 *dq = prm.Dc32 + (size_t)q * K;
-#pragma unroll 6
-                    for (int kk = part; kk < K; kk += 4) {
-                        const float2 d = __ldg(dq + kk), z = __ldg(zr + kk);
-                        acc = fmaf(d.x, z.x, acc);
-                        acc = fmaf(-d.y, z.y, acc);
+                    for (int k0 = 0; k0 < K; k0 += 64) {
+                        float2 d[16], z[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int kk = k0 + part + 4 * u;
+                            d[u] = kk < K ? __ldg(dq + kk) : make_float2(0.f, 0.f);
+                            z[u] = kk < K ? __ldg(zr + kk) : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            if (k0 + part + 4 * u < K) {
+                                acc = fmaf(d[u].x, z[u].x, acc);
+                                acc = fmaf(-d[u].y, z[u].y, acc);
+                            }
+                        }
                     }
                 }
                 acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -918,18 +931,17 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                     bq = q;
                 }
             }
-            // best over the 4 candidate groups of this half-warp
-#pragma unroll
-            for (int o = 4; o < 16; o <<= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+            // best over the 2 candidate groups of this 8-lane group
+            {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, 4);
+                const int oq = __shfl_xor_sync(0xffffffffu, bq, 4);
                 const bool take = (bq < 0) || (oq >= 0 && (ov > best || (ov == best && oq < bq)));
                 if (take) {
                     best = ov;
                     bq = oq;
                 }
             }
-            if ((lane & 15) == 0 && live) {
+            if ((lane & 7) == 0 && live) {
                 prm.idx[frame] = bq;
                 if (prm.proj) prm.proj[frame] = bq < 0 ? __int_as_float(0x7fc00000) : best;
             }
