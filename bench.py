@@ -243,7 +243,7 @@ def bench_array3d(sp, I, torch, unique=C4_UNIQUE, repeat=C4_REPEAT):
         "svd_kdtree_fp16_frames_per_s": T / t_kd * 1000,
         "ms_per_pass": {"svd_proj_kernel": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
                         "mlp_tc_kernel": t_mlp, "rescore_and_fallback_scan": t_lrn_ns - t_proj - t_mlp,
-                        "score_row_kernel": t_exh - t_exh_ns, "kdtree": t_kd - (t_exh - t_exh_ns) - t_proj},
+                        "step4_bulk_kernel": t_exh - t_exh_ns, "kdtree": t_kd - (t_exh - t_exh_ns) - t_proj},
         "learned": {"n_top": LEARNED_N_TOP, "theta": LEARNED_THETA, "cells": 642, "hidden": [256, 256],
                     "train_frames": 65536, "epochs": 6, "train_s": train_s,
                     "final_loss": float(losses[-1]),
