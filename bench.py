@@ -254,6 +254,67 @@ def bench_array3d(sp, I, torch, unique=C4_UNIQUE, repeat=C4_REPEAT):
     return out
 
 
+C5_UNIQUE, C5_REPEAT, C5_TRAIN = 8192, 8, 16384
+
+
+def bench_c5(sp, I, torch):
+    """The 16-mic array in a 5 cm-radius ball (the one of the ball16_n1024_q642 parity
+    cases), N = 1024 (B = 513, P = 120, L = 61,560), on the level-6 grid (Q = 40,962): the
+    exhaustive FP16 path and the learned proposal (level-3 cells, top-4 cells of ~64
+    children each) on 65,536 frames per pass (8,192 unique frames of 1-3 white sources in
+    white noise at -5..20 dB, repeated 8 times on the device).  No FP64 oracle exists at this
+    size (its basis needs the eigendecomposition of a 40,962 x 40,962 Gram), so agreement is
+    reported against the library's own FP32 exhaustive path on the unique frames."""
+    fs, c, N = 16000.0, 343.0, 1024
+    mic = I.array_random_ball(np.random.default_rng([I.SEED_BASE + 7, 4]), 16)
+    dirs = I.icosphere(6)
+    t0 = time.perf_counter()
+    st = sp.build_steering(mic, dirs, fs, c, N)
+    b = sp.svd_reduce(st, 1e-5)
+    torch.cuda.synchronize()
+    basis_s = time.perf_counter() - t0
+    rng = np.random.default_rng(I.SEED_BASE + 60)
+    ev, _, _ = I.training_frames(rng, mic, C5_UNIQUE, N, fs, c)
+    uniq = torch.from_numpy(ev).cuda()
+    del ev
+    frames = uniq.repeat(C5_REPEAT, 1, 1)
+    T = frames.shape[0]
+    tr, _, _ = I.training_frames(np.random.default_rng(I.SEED_BASE + 61), mic, C5_TRAIN, N, fs, c)
+    p = sp.Proposal(b, I.icosphere(3), seed=5)
+    x, y = p.examples(torch.from_numpy(tr).cuda(), "fp16")
+    del tr
+    t1 = time.perf_counter()
+    losses = p.train(x, y, epochs=6, batch=512, lr=1e-3, seed=6)
+    train_s = time.perf_counter() - t1
+    del x, y
+
+    ex16 = sp.localize(b, uniq, "svd_exhaustive", "fp16", score=False)[0]
+    ex32 = sp.localize(b, uniq, "svd_exhaustive", "fp32", score=False)[0]
+    li, _, _, fb = p.localize(uniq, "fp16", n_top=4, theta=LEARNED_THETA, score=False)
+    torch.cuda.synchronize()
+    ms = lambda fn, n: T / _rate(fn, n, T, torch) * 1000
+    t_proj = ms(lambda: sp.project(b, frames, "fp16"), 3)
+    t_exh = ms(lambda: sp.localize(b, frames, "svd_exhaustive", "fp16"), 3)
+    t_exh_ns = ms(lambda: sp.localize(b, frames, "svd_exhaustive", "fp16", score=False), 3)
+    t_lrn = ms(lambda: p.localize(frames, "fp16", n_top=4, theta=LEARNED_THETA, fallback=False), 3)
+    return {
+        "workload": f"ball16_n1024_q40962: 16-mic array in a 5 cm-radius ball, N=1024, Q=40962, K={b.K}, "
+                    f"{T} frames per pass ({C5_UNIQUE} unique x {C5_REPEAT}), 1-3 white sources, white noise "
+                    f"-5..20 dB (no reverberation)",
+        "svd_exhaustive_fp16_frames_per_s": T / t_exh * 1000,
+        "svd_learned_fp16_frames_per_s": T / t_lrn * 1000,
+        "ms_per_pass": {"svd_proj_kernel": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
+                        "step4": t_exh - t_exh_ns, "learned_total": t_lrn},
+        "gemm1_hbm_GBps": 8 * 16 * 513 * T / (t_proj * 1e-3) / 1e9,
+        "fp16_agreement_vs_fp32_path": float((ex16 == ex32).float().mean()),
+        "learned": {"n_top": 4, "theta": LEARNED_THETA, "cells": 642, "train_frames": C5_TRAIN, "epochs": 6,
+                    "train_s": train_s, "final_loss": float(losses[-1]),
+                    "fallback_fraction": float(fb.float().mean()),
+                    "agreement_vs_exhaustive_fp16": float((li == ex16).float().mean())},
+        "basis_setup_s": basis_s,
+    }
+
+
 N_STREAMS, N_CONFIGS = 256, 16
 
 
@@ -319,7 +380,7 @@ def main():
     ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16"])
     ap.add_argument("--frames", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the SRP / precision comparison lines")
-    ap.add_argument("--only", choices=["array3d", "batched"], default=None,
+    ap.add_argument("--only", choices=["array3d", "batched", "c5"], default=None,
                     help="run only one extra section and print its JSON (profiling runs)")
     ap.add_argument("--array3d-frames", type=int, default=C4_UNIQUE,
                     help="unique frames of the 3-D array section (repeated to 2^20 unless --only)")
@@ -345,6 +406,8 @@ def main():
     if args.only is not None:
         if args.only == "array3d":
             print(json.dumps(bench_array3d(sp, I, torch, args.array3d_frames, 1)), flush=True)
+        elif args.only == "c5":
+            print(json.dumps(bench_c5(sp, I, torch)), flush=True)
         else:
             print(json.dumps(bench_batched(sp, I, torch)), flush=True)
         return

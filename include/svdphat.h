@@ -234,8 +234,8 @@ int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode 
  * which every GPU that loads the library holds until the process exits.
  *
  * prec: SP_PREC_FP16 or SP_PREC_BF16 (SP_ENOTIMPL otherwise).  A call needs
- * T * (8 K + 4) bytes of that scratch (K from sp_svd_reduce; at K = 48 that is up to
- * 21,000 frames per call); larger T is rejected with SP_EINVAL before any work is queued.
+ * about T * (8 K + 16) bytes of that scratch (K from sp_svd_reduce; at K = 48 that is up to
+ * 20,900 frames per call); larger T is rejected with SP_EINVAL before any work is queued.
  * idx_dev, score_dev, proj_score_dev: as for sp_localize.  The caller still provides the
  * frames and all outputs.
  *

@@ -274,10 +274,12 @@ int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
             } else {
                 SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "bad precision");
                 const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
-                SP_TRY(work.reserve(zbytes + (size_t)T * 4));
+                const size_t nbytes = ((size_t)T * 4 + 255) / 256 * 256;
+                SP_TRY(work.reserve(zbytes + nbytes + scan_workspace_bytes(T)));
                 float *zn2 = reinterpret_cast<float *>(work.as<char>() + zbytes);
                 SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, zn2, s, max_ctas));
-                SP_TRY(launch_svd_scan(b, work.p, zn2, T, (int)prec, idx_dev, proj_score_dev, s));
+                SP_TRY(launch_svd_scan(b, work.p, zn2, T, (int)prec, idx_dev, proj_score_dev, s,
+                                       work.as<char>() + zbytes + nbytes));
             }
             break;
         }

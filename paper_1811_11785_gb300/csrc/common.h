@@ -166,6 +166,8 @@ int launch_phat(const void *frames, int T, int M, int B, void *x, cudaStream_t s
 int launch_srp_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint64_t *keys,
                       int32_t *idx, float *best, cudaStream_t s);
 int launch_project_f32(const sp_basis *b, const void *X, int T, void *Z, cudaStream_t s);
+int launch_svd_scan_f32_list(const sp_basis *b, const void *Z, int T_cap, const int *count, const int32_t *list,
+                             uint64_t *keys, int32_t *idx, float *best, cudaStream_t s);
 int launch_svd_scan_f32(const sp_basis *b, const void *Z, int T, uint64_t *keys, int32_t *idx,
                         float *best, cudaStream_t s);
 int launch_score_row(const sp_steering *st, const void *frames, int T, const int32_t *idx,
@@ -176,8 +178,11 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
 // (zn2_out [T] receives ||Z||^2 per frame, may be null; the scan needs it)
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
                     cudaStream_t s, int max_ctas = 0);
+// ws: scan_workspace_bytes(T) bytes, 256-byte aligned (list of the frames whose candidate
+// window overflows, their keys and a count).
+size_t scan_workspace_bytes(int T);
 int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
-                    float *proj, cudaStream_t s);
+                    float *proj, cudaStream_t s, void *ws);
 int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
                   cudaStream_t s);
 int tc_prepare(sp_basis *b);

@@ -56,9 +56,10 @@ extern "C" int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, in
     SP_CHECK(reinterpret_cast<uintptr_t>(frames_dev) % 8 == 0 && reinterpret_cast<uintptr_t>(idx_dev) % 4 == 0,
              SP_EINVAL, "sp_localize_noalloc: misaligned pointer");
     const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
-    const size_t need = zbytes + (size_t)T * 4;
+    const size_t nbytes = ((size_t)T * 4 + 255) / 256 * 256;
+    const size_t need = zbytes + nbytes + scan_workspace_bytes(T);
     SP_CHECK(need <= kNoAllocBytes, SP_EINVAL,
-             "sp_localize_noalloc: T * (8 K + 4) bytes of scratch exceeds the built-in 8 MiB (" +
+             "sp_localize_noalloc: about T * (8 K + 16) bytes of scratch exceeds the built-in 8 MiB (" +
                  std::to_string(need) + " bytes requested)");
     void *scratch = nullptr;
     SP_TRY(noalloc_scratch(&scratch));
@@ -66,7 +67,7 @@ extern "C" int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, in
     float *zn2 = reinterpret_cast<float *>(z + zbytes);
     cudaStream_t s = (cudaStream_t)stream;
     SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, z, zn2, s));
-    SP_TRY(launch_svd_scan(b, z, zn2, T, (int)prec, idx_dev, proj_score_dev, s));
+    SP_TRY(launch_svd_scan(b, z, zn2, T, (int)prec, idx_dev, proj_score_dev, s, z + zbytes + nbytes));
     if (score_dev) SP_TRY(launch_score_row(b->st, frames_dev, T, idx_dev, score_dev, s));
     return SP_OK;
 }

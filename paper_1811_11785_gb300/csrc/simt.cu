@@ -86,111 +86,134 @@ __global__ void finalize_keys_kernel(const unsigned long long *__restrict__ keys
 
 // ------------------------------------------------------------------------- Re{A X} + argmax
 // Y[q][t] = sum_l Re(A[q][l] X[t][l]) = sum_l (Ar Xr - Ai Xi) over a contraction of Lc
-// complex entries; a 128 q x 128 t tile per CTA, 8 x 8 outputs per thread, K step of 8
+// complex entries; a 128 q x 128 t tile per item, 8 x 8 outputs per thread, K step of 8
 // complex entries double-buffered through shared memory.  The tile's best (score, q) per
-// frame is merged across CTAs with a 64-bit atomicMax on the packed key.
+// frame is merged across items with a 64-bit atomicMax on the packed key.
+// List mode (count != null): the rows of X are list[0 .. *count), read from device memory
+// when the kernel starts, and keys are indexed by list position; CTAs stride over the
+// (q tile, t tile) items, so an empty list costs one read per CTA.
 constexpr int RA_M = 128, RA_N = 128, RA_K = 8;
 
 __global__ void __launch_bounds__(256, 2)
-    re_argmax_kernel(const float2 *__restrict__ A, int Qa, int Lc, const float2 *__restrict__ X, int T,
-                     int nq, unsigned long long *__restrict__ keys) {
+    re_argmax_kernel(const float2 *__restrict__ A, int Qa, int Lc, const float2 *__restrict__ X, int T_in,
+                     int nq, unsigned long long *__restrict__ keys, const int32_t *__restrict__ list,
+                     const int *__restrict__ count) {
     __shared__ __align__(16) float As[2][2 * RA_K][RA_M + 4];
     __shared__ __align__(16) float Bs[2][2 * RA_K][RA_N + 4];
     const int tid = threadIdx.x;
-    const long long blk = blockIdx.x;
-    const int q0 = (int)(blk % nq) * RA_M;
-    const long long t0 = (blk / nq) * RA_N;
-    const int lr = tid >> 1, lk = (tid & 1) * 4;   // load mapping: row, first complex column
-    const int ty = tid >> 4, tx = tid & 15;         // compute mapping
+    const int T = count ? *count : T_in;
+    const long long n_items = (long long)nq * (((long long)T + RA_N - 1) / RA_N);
+    for (long long blk = blockIdx.x; blk < n_items; blk += gridDim.x) {
+        const int q0 = (int)(blk % nq) * RA_M;
+        const long long t0 = (blk / nq) * RA_N;
+        const int lr = tid >> 1, lk = (tid & 1) * 4;   // load mapping: row, first complex column
+        const int ty = tid >> 4, tx = tid & 15;         // compute mapping
 
-    const bool a_ok = q0 + lr < Qa;
-    const bool b_ok = t0 + lr < T;
-    const float2 *arow = A + (size_t)(a_ok ? q0 + lr : 0) * Lc;
-    const float2 *brow = X + (size_t)(b_ok ? t0 + lr : 0) * Lc;
+        const bool a_ok = q0 + lr < Qa;
+        const bool b_ok = t0 + lr < T;
+        const float2 *arow = A + (size_t)(a_ok ? q0 + lr : 0) * Lc;
+        const long long brow_i = b_ok ? (list ? (long long)list[t0 + lr] : t0 + lr) : 0;
+        const float2 *brow = X + (size_t)brow_i * Lc;
 
-    float2 ra[4], rb[4];
-    auto gload = [&](int k0) {
+        float2 ra[4], rb[4];
+        auto gload = [&](int k0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = k0 + lk + i;
-            ra[i] = (a_ok && k < Lc) ? __ldg(arow + k) : make_float2(0.f, 0.f);
-            rb[i] = (b_ok && k < Lc) ? __ldg(brow + k) : make_float2(0.f, 0.f);
-        }
-    };
-    auto sstore = [&](int buf) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            As[buf][2 * (lk + i)][lr] = ra[i].x;
-            As[buf][2 * (lk + i) + 1][lr] = ra[i].y;
-            Bs[buf][2 * (lk + i)][lr] = rb[i].x;
-            Bs[buf][2 * (lk + i) + 1][lr] = rb[i].y;
-        }
-    };
-
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-
-    gload(0);
-    sstore(0);
-    __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < Lc; k0 += RA_K) {
-        const bool more = k0 + RA_K < Lc;
-        if (more) gload(k0 + RA_K);
-#pragma unroll
-        for (int kk = 0; kk < RA_K; ++kk) {
-            float ar[8], ai[8], br[8], bi[8];
-            *(float4 *)&ar[0] = *(const float4 *)&As[buf][2 * kk][ty * 4];
-            *(float4 *)&ar[4] = *(const float4 *)&As[buf][2 * kk][64 + ty * 4];
-            *(float4 *)&ai[0] = *(const float4 *)&As[buf][2 * kk + 1][ty * 4];
-            *(float4 *)&ai[4] = *(const float4 *)&As[buf][2 * kk + 1][64 + ty * 4];
-            *(float4 *)&br[0] = *(const float4 *)&Bs[buf][2 * kk][tx * 4];
-            *(float4 *)&br[4] = *(const float4 *)&Bs[buf][2 * kk][64 + tx * 4];
-            *(float4 *)&bi[0] = *(const float4 *)&Bs[buf][2 * kk + 1][tx * 4];
-            *(float4 *)&bi[4] = *(const float4 *)&Bs[buf][2 * kk + 1][64 + tx * 4];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
-                    acc[i][j] = fmaf(-ai[i], bi[j], acc[i][j]);
-                }
-        }
-        if (more) sstore(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-    }
-
-    // per-thread best over its 8 q rows (ascending q), for each of its 8 frames
-    unsigned long long *red = reinterpret_cast<unsigned long long *>(&As[0][0][0]);  // [16][128]
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int tcol = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-        unsigned long long best = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int q = q0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-            const float v = acc[i][j];
-            if (q < Qa && !isnan(v)) {
-                const unsigned long long key = pack_key(v, q);
-                best = key > best ? key : best;
+            for (int i = 0; i < 4; ++i) {
+                const int k = k0 + lk + i;
+                ra[i] = (a_ok && k < Lc) ? __ldg(arow + k) : make_float2(0.f, 0.f);
+                rb[i] = (b_ok && k < Lc) ? __ldg(brow + k) : make_float2(0.f, 0.f);
             }
-        }
-        red[ty * RA_N + tcol] = best;
-    }
-    __syncthreads();
-    if (tid < RA_N) {
-        unsigned long long best = 0;
+        };
+        auto sstore = [&](int buf) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const unsigned long long k = red[r * RA_N + tid];
-            best = k > best ? k : best;
+            for (int i = 0; i < 4; ++i) {
+                As[buf][2 * (lk + i)][lr] = ra[i].x;
+                As[buf][2 * (lk + i) + 1][lr] = ra[i].y;
+                Bs[buf][2 * (lk + i)][lr] = rb[i].x;
+                Bs[buf][2 * (lk + i) + 1][lr] = rb[i].y;
+            }
+        };
+
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+        gload(0);
+        sstore(0);
+        __syncthreads();
+        int buf = 0;
+        for (int k0 = 0; k0 < Lc; k0 += RA_K) {
+            const bool more = k0 + RA_K < Lc;
+            if (more) gload(k0 + RA_K);
+#pragma unroll
+            for (int kk = 0; kk < RA_K; ++kk) {
+                float ar[8], ai[8], br[8], bi[8];
+                *(float4 *)&ar[0] = *(const float4 *)&As[buf][2 * kk][ty * 4];
+                *(float4 *)&ar[4] = *(const float4 *)&As[buf][2 * kk][64 + ty * 4];
+                *(float4 *)&ai[0] = *(const float4 *)&As[buf][2 * kk + 1][ty * 4];
+                *(float4 *)&ai[4] = *(const float4 *)&As[buf][2 * kk + 1][64 + ty * 4];
+                *(float4 *)&br[0] = *(const float4 *)&Bs[buf][2 * kk][tx * 4];
+                *(float4 *)&br[4] = *(const float4 *)&Bs[buf][2 * kk][64 + tx * 4];
+                *(float4 *)&bi[0] = *(const float4 *)&Bs[buf][2 * kk + 1][tx * 4];
+                *(float4 *)&bi[4] = *(const float4 *)&Bs[buf][2 * kk + 1][64 + tx * 4];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+                        acc[i][j] = fmaf(-ai[i], bi[j], acc[i][j]);
+                    }
+            }
+            if (more) sstore(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
         }
-        const long long t = t0 + tid;
-        if (t < T && best) atomicMax(keys + t, best);
+
+        // per-thread best over its 8 q rows (ascending q), for each of its 8 frames
+        unsigned long long *red = reinterpret_cast<unsigned long long *>(&As[0][0][0]);  // [16][128]
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int tcol = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+            unsigned long long best = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int q = q0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+                const float v = acc[i][j];
+                if (q < Qa && !isnan(v)) {
+                    const unsigned long long key = pack_key(v, q);
+                    best = key > best ? key : best;
+                }
+            }
+            red[ty * RA_N + tcol] = best;
+        }
+        __syncthreads();
+        if (tid < RA_N) {
+            unsigned long long best = 0;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const unsigned long long k = red[r * RA_N + tid];
+                best = k > best ? k : best;
+            }
+            const long long t = t0 + tid;
+            if (t < T && best) atomicMax(keys + t, best);
+        }
+        __syncthreads();   // the next item reuses the shared tiles
+    }
+}
+
+// List mode's results: frame list[r] gets the argmax (through remap) and score of keys[r].
+__global__ void finalize_list_kernel(const unsigned long long *__restrict__ keys, const int *__restrict__ count,
+                                     const int32_t *__restrict__ list, const int32_t *__restrict__ remap,
+                                     int32_t *__restrict__ idx, float *__restrict__ best) {
+    const int n = *count;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[r];
+        const int t = list[r];
+        const int32_t q = (int32_t)(~(uint32_t)k);
+        idx[t] = k ? (remap ? remap[q] : q) : -1;
+        if (best) best[t] = k ? key_score(k) : __int_as_float(0x7fc00000);
     }
 }
 
@@ -202,7 +225,7 @@ static int launch_re_argmax(const void *A, int Qa, int Lc, const void *X, int T,
     const long long nt = ((long long)T + RA_N - 1) / RA_N;
     re_argmax_kernel<<<(unsigned)(nq * nt), 256, 0, s>>>((const float2 *)A, Qa, Lc,
                                                           (const float2 *)X, T, nq,
-                                                          (unsigned long long *)keys);
+                                                          (unsigned long long *)keys, nullptr, nullptr);
     SP_CUDA(cudaGetLastError());
     finalize_keys_kernel<<<(T + 255) / 256, 256, 0, s>>>((const unsigned long long *)keys, T, remap, idx, best);
     SP_CUDA(cudaGetLastError());
@@ -215,6 +238,25 @@ int launch_srp_argmax(const void *A, int Qa, int Lc, const void *X, int T, uint6
 }
 
 // FP32 exhaustive scan Re{D Z} (Eq. 14) over the class representatives only.
+// The same FP32 scan for the frames list[0 .. *count) of Z (count on the device, at most
+// T_cap); keys[0 .. *count) must be zero.  Writes idx / best of the listed frames only.
+int launch_svd_scan_f32_list(const sp_basis *b, const void *Z, int T_cap, const int *count, const int32_t *list,
+                             uint64_t *keys, int32_t *idx, float *best, cudaStream_t s) {
+    if (T_cap == 0) return SP_OK;
+    const int Qa = (int)b->st->reps.size();
+    const int nq = (Qa + RA_M - 1) / RA_M;
+    const long long items = (long long)nq * (((long long)T_cap + RA_N - 1) / RA_N);
+    const unsigned grid = (unsigned)std::min<long long>(items, 2LL * num_sms());
+    re_argmax_kernel<<<grid, 256, 0, s>>>(b->Dc32r.as<float2>(), Qa, b->K, (const float2 *)Z, T_cap, nq,
+                                          (unsigned long long *)keys, list, count);
+    SP_CUDA(cudaGetLastError());
+    const unsigned fgrid = (unsigned)std::min<long long>(((long long)T_cap + 255) / 256, num_sms());
+    finalize_list_kernel<<<fgrid, 256, 0, s>>>((const unsigned long long *)keys, count, list,
+                                               b->st->d_reps.as<int32_t>(), idx, best);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
 int launch_svd_scan_f32(const sp_basis *b, const void *Z, int T, uint64_t *keys, int32_t *idx,
                         float *best, cudaStream_t s) {
     return launch_re_argmax(b->Dc32r.p, (int)b->st->reps.size(), b->K, Z, T, keys, b->st->d_reps.as<int32_t>(),

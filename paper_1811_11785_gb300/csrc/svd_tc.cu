@@ -713,6 +713,9 @@ struct ScanParams {
     const float2 *Dc32;  // [Q][K] complex64
     float tol_z;         // 2 * 2.1 u sqrt(L): candidate window per unit ||Z||
     float tol_abs;       // 2 * 1e-6 L
+    int *ovf_count;      // frames whose window holds more than kCap classes: count, list,
+    int32_t *ovf_list;   // and their argmax keys (zeroed here), for the FP32 list scan
+    unsigned long long *ovf_keys;
     int32_t *idx;
     float *proj;
 };
@@ -894,7 +897,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             const long long frame = t0 + r;
             const bool live = frame < T;
             const int n = live ? cnt_s[r] : 0;
-            const int total = n <= kCap ? n : prm.Qr;   // n > kCap: every class
+            const int total = n <= kCap ? n : 0;   // n > kCap: the FP32 list scan takes the frame
             const float2 *zr = prm.Z + (size_t)(live ? frame : 0) * K;
             float best = 0.f;
             int bq = -1;
@@ -942,8 +945,14 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 }
             }
             if ((lane & 7) == 0 && live) {
-                prm.idx[frame] = bq;
-                if (prm.proj) prm.proj[frame] = bq < 0 ? __int_as_float(0x7fc00000) : best;
+                if (n > kCap) {
+                    const int pos = atomicAdd(prm.ovf_count, 1);
+                    prm.ovf_list[pos] = (int32_t)frame;
+                    prm.ovf_keys[pos] = 0ull;
+                } else {
+                    prm.idx[frame] = bq;
+                    if (prm.proj) prm.proj[frame] = bq < 0 ? __int_as_float(0x7fc00000) : best;
+                }
             }
         }
     }
@@ -1147,9 +1156,12 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     return SP_OK;
 }
 
+size_t scan_workspace_bytes(int T) { return 256 + ((size_t)T * 4 + 255) / 256 * 256 + (size_t)T * 8; }
+
 int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
-                    float *proj, cudaStream_t s) {
+                    float *proj, cudaStream_t s, void *ws) {
     if (T == 0) return SP_OK;
+    SP_CHECK(ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, SP_EINVAL, "scan: workspace missing or misaligned");
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
              "tensor-core path supports 2K <= 320 and M <= 16 (use SP_PREC_FP32)");
@@ -1172,6 +1184,11 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     p.tol_abs = (float)(2.0 * 1e-6 * L);
     p.idx = idx;
     p.proj = proj;
+    char *w = static_cast<char *>(ws);
+    p.ovf_count = reinterpret_cast<int *>(w);
+    p.ovf_list = reinterpret_cast<int32_t *>(w + 256);
+    p.ovf_keys = reinterpret_cast<unsigned long long *>(w + 256 + ((size_t)T * 4 + 255) / 256 * 256);
+    SP_CUDA(cudaMemsetAsync(p.ovf_count, 0, sizeof(int), s));
     // four D tiles in flight, two when the Z tile and four D tiles would not fit (2K > 256)
     const int ring = 3 * t.k2_atoms * kAtomBytes + 128 * kCap * 4 <= 216 * 1024 ? kRingMax : 2;
     const int smem = t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 128 * kCap * 4 + 128 * 4 +
@@ -1189,7 +1206,9 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     const unsigned grid = (unsigned)(((long long)T + 127) / 128);
     kern<<<grid, kScanThreads, smem, s>>>(maps->d[bf], p);
     SP_CUDA(cudaGetLastError());
-    return SP_OK;
+    // frames with more than kCap classes in their window: the exact FP32 scan over every class
+    return launch_svd_scan_f32_list(b, Z, T, p.ovf_count, p.ovf_list, reinterpret_cast<uint64_t *>(p.ovf_keys), idx,
+                                    proj, s);
 }
 
 }  // namespace sp

@@ -265,6 +265,28 @@ def test_zero_and_nan_frames():
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_window_overflow_frames_take_the_fp32_list_scan(prec):
+    """A silent frame (Z = 0) ties every class, so its candidate window overflows and the
+    frame is scored by the FP32 scan over every class on the compacted list: its index is the
+    lowest direction (Eq. 14 with ties to the lowest index) and its projection score 0, while
+    the other frames of the batch come out exactly as without the silent ones."""
+    d = _setup("planar_q2562", 777)
+    fr = d["frames"][:600].clone()
+    silent = torch.arange(3, 600, 7, device=fr.device)
+    fr[silent] = 0
+    idx, score, proj = sp.localize(d["b"], fr, "svd_exhaustive", prec)
+    ref_i, ref_s, ref_p = sp.localize(d["b"], d["frames"][:600].contiguous(), "svd_exhaustive", prec)
+    torch.cuda.synchronize()
+    sp.check_status()
+    keep = torch.ones(600, dtype=torch.bool, device=fr.device)
+    keep[silent] = False
+    assert torch.equal(idx[keep], ref_i[keep])
+    assert torch.equal(proj[keep], ref_p[keep]) and torch.equal(score[keep], ref_s[keep])
+    assert bool((idx[silent] == 0).all())
+    assert float(proj[silent].abs().max()) == 0.0 and float(score[silent].abs().max()) == 0.0
+
+
 def test_host_path_matches_device():
     d = _setup("planar_q2562", 777)
     fh = d["frames"].cpu().pin_memory()

@@ -57,7 +57,7 @@ def test_noalloc_matches_localize_two_calls_in_a_row(setup, prec):
 
 def test_noalloc_rejects_batches_beyond_its_scratch(setup):
     st, b, frames = setup
-    big = 8 * 2 ** 20 // (8 * b.K + 4) + 1   # one frame more than the built-in array holds
+    big = 8 * 2 ** 20 // (8 * b.K + 16) + 1   # more frames than the built-in array holds
     idx = torch.empty(1, dtype=torch.int32, device="cuda")
     rc = sp.lib().sp_localize_noalloc(b.handle, ctypes.c_void_p(frames.data_ptr()), big, sp.PREC["fp16"],
                                       ctypes.c_void_p(idx.data_ptr()), None, None, None)
