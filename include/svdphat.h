@@ -191,9 +191,11 @@ int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
  * mode SP_MODE_SVD_EXHAUSTIVE: idx = argmax_q Re{D_q Z} (Eq. 14).  With FP16/BF16 the
  *                              reduced-precision scan collects, per frame, every class
  *                              whose score lies within the scan's rounding bound of the
- *                              frame's maximum (at most 16, else all classes) and
- *                              rescores them in FP32 against FP32 Z and D, so the result
- *                              equals an FP32 scan of the same Z.
+ *                              frame's maximum and rescores them in FP32 against FP32 Z
+ *                              and D; a frame with more than 16 such classes is scored in
+ *                              FP32 against every class instead.  Either way the result
+ *                              equals an FP32 scan of the same Z (up to FP32 summation
+ *                              order).
  * mode SP_MODE_SVD_KDTREE:     idx = nearest D^_q to conj(Z/||Z||) by exact k-d tree
  *                              search (Eq. 15), FP32 distances.
  *
