@@ -92,6 +92,22 @@ int sp_version(void);
 int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q,
                       double fs, double c, int N, int flags, sp_steering **out);
 
+/* The same offline step for sources at given positions (the near field, Eq. 1; Section 2
+ * gives Eq. 2 as its limit for a source far from a small array, and Section 6 names the
+ * near-field effect as an extension):
+ *   tau[q][p] = fs/c * (||s_q - r_i|| - ||s_q - r_j||),  pair p = (i, j), i < j,
+ * with src_xyz the Q x 3 candidate source positions in metres, in the microphones'
+ * frame.  Computed on the device in FP64 with every norm in the fixed order
+ * sqrt((ex*ex + ey*ey) + ez*ez), e = s - r, then tau = (fs/c) * (n_i - n_j), each step
+ * correctly rounded.  Everything downstream (W, direction classes, sp_svd_reduce, every
+ * sp_localize mode, step 4 with d_m = -fs/c ||s_q - r_m||) is the same as for directions.
+ * A source at the coordinate origin is SP_EINVAL (s_q / ||s_q|| is the direction used to
+ * assign learned-proposal cells); other arguments and errors as for sp_build_steering.
+ * sp_steering_nearfield reports which builder made a handle (1 near field, 0 directions). */
+int sp_build_steering_nearfield(const double *mic_xyz, int M, const double *src_xyz, int Q,
+                                double fs, double c, int N, int flags, sp_steering **out);
+int sp_steering_nearfield(const sp_steering *st, int *nearfield);
+
 /* Dimensions of a steering handle; any pointer may be NULL. */
 int sp_steering_dims(const sp_steering *st, int *M, int *P, int *Q, int *N, int *B);
 
@@ -148,13 +164,14 @@ void sp_basis_destroy(sp_basis *b);
  *
  * sp_save_basis writes b to path (a new file, or overwritten): a little-endian binary
  * with an 80-byte header (magic "SVDPHAT1", version 1, M, Q, N, K, number of singular
- * values, fs, c, delta), the FP64 arrays mic [M][3], dirs [Q][3], sigma^2, V [L][K] and
+ * values, the steering model (0 directions, 1 source positions), fs, c, delta), the FP64
+ * arrays mic [M][3], dirs or source positions [Q][3], sigma^2, V [L][K] and
  * D [Q][K] (complex as re, im pairs), and an FNV-1a 64 checksum of all preceding bytes.
  * Returns SP_EINVAL if the file cannot be opened or written.
  *
- * sp_load_basis reads such a file, rebuilds the steering handle (flags as in
- * sp_build_steering: SP_STEER_MATERIALIZE_W or 0), the device operands and the k-d tree
- * on the current device, and returns a basis that OWNS its steering handle (released by
+ * sp_load_basis reads such a file, rebuilds the steering handle with the builder of its
+ * model (flags as in sp_build_steering: SP_STEER_MATERIALIZE_W or 0), the device operands
+ * and the k-d tree on the current device, and returns a basis that OWNS its steering handle (released by
  * sp_basis_destroy; obtain it with sp_basis_steering, never destroy it separately).
  * Results through a loaded basis are bit-identical to those through the saved one.
  * A malformed file (wrong magic or version, sizes out of range, a length that does not

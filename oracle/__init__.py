@@ -99,12 +99,26 @@ def tdoa_farfield(mic_xyz, dirs, fs: float, c: float) -> np.ndarray:
 
 
 def tdoa_nearfield(mic_xyz, src_xyz, fs: float, c: float) -> np.ndarray:
-    """Eq. 1 (near field): ``tau[q, p] = fs/c * (||s_q - r_i|| - ||s_q - r_j||)``."""
+    """Eq. 1 (near field): ``tau[q, p] = fs/c * (||s_q - r_i|| - ||s_q - r_j||)`` in samples,
+    for source positions ``s_q``.
+
+    Evaluation order is fixed so the table is reproducible to the last bit:
+    ``n_m = sqrt((ex*ex + ey*ey) + ez*ez)`` with ``e = s_q - r_m``, then
+    ``tau = (fs / c) * (n_i - n_j)``; every operation rounds to nearest, no fused
+    multiply-add.
+    """
     r = np.asarray(mic_xyz, dtype=np.float64)
     s = np.asarray(src_xyz, dtype=np.float64)
-    dist = np.sqrt(((s[:, None, :] - r[None, :, :]) ** 2).sum(-1))  # (Q, M)
+    dist = np.empty((s.shape[0], r.shape[0]), dtype=np.float64)
+    for m in range(r.shape[0]):
+        ex, ey, ez = s[:, 0] - r[m, 0], s[:, 1] - r[m, 1], s[:, 2] - r[m, 2]
+        dist[:, m] = np.sqrt((ex * ex + ey * ey) + ez * ez)
+    g = np.float64(fs) / np.float64(c)
     P = pairs(r.shape[0])
-    return (fs / c) * np.stack([dist[:, i] - dist[:, j] for (i, j) in P], axis=1)
+    tau = np.empty((s.shape[0], len(P)), dtype=np.float64)
+    for p, (i, j) in enumerate(P):
+        tau[:, p] = g * (dist[:, i] - dist[:, j])
+    return tau
 
 
 def steering(tau: np.ndarray, N: int) -> np.ndarray:

@@ -38,6 +38,9 @@ _SIGS = {
     "sp_version": ([], ctypes.c_int),
     "sp_build_steering": ([_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+    "sp_build_steering_nearfield": ([_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+    "sp_steering_nearfield": ([_vp, _ip], ctypes.c_int),
     "sp_steering_dims": ([_vp, _ip, _ip, _ip, _ip, _ip], ctypes.c_int),
     "sp_steering_classes": ([_vp, _ip, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "sp_steering_tau": ([_vp, _dp], ctypes.c_int),
@@ -139,17 +142,19 @@ def _frames(frames, st):
 
 
 class Steering:
-    """TDOA table and steering matrix W (Eq. 2, 4, 8) on the device."""
+    """TDOA table and steering matrix W (Eq. 2, 4, 8) on the device; with nearfield=True
+    ``dirs`` are source positions and the TDOA follows Eq. 1."""
 
-    def __init__(self, mic_xyz, dirs, fs: float, c: float, N: int, materialize_w: bool = False):
+    def __init__(self, mic_xyz, dirs, fs: float, c: float, N: int, materialize_w: bool = False,
+                 nearfield: bool = False):
         L = lib()
         mic = np.ascontiguousarray(mic_xyz, dtype=np.float64)
         d = np.ascontiguousarray(dirs, dtype=np.float64)
         h = _vp()
-        _check("sp_build_steering",
-               L.sp_build_steering(mic.ctypes.data_as(_dp), mic.shape[0], d.ctypes.data_as(_dp), d.shape[0],
-                                   float(fs), float(c), int(N),
-                                   STEER_MATERIALIZE_W if materialize_w else 0, ctypes.byref(h)))
+        fn = "sp_build_steering_nearfield" if nearfield else "sp_build_steering"
+        _check(fn, getattr(L, fn)(mic.ctypes.data_as(_dp), mic.shape[0], d.ctypes.data_as(_dp), d.shape[0],
+                                  float(fs), float(c), int(N), STEER_MATERIALIZE_W if materialize_w else 0,
+                                  ctypes.byref(h)))
         self._h = h
         self._owned = True
         self._dims()
@@ -170,6 +175,9 @@ class Steering:
         _check("sp_steering_dims", lib().sp_steering_dims(self._h, *[ctypes.byref(x) for x in v]))
         self.M, self.P, self.Q, self.N, self.B = (x.value for x in v)
         self.L = self.P * self.B
+        nf = ctypes.c_int()
+        _check("sp_steering_nearfield", lib().sp_steering_nearfield(self._h, ctypes.byref(nf)))
+        self.nearfield = bool(nf.value)
 
     @property
     def handle(self):
@@ -268,6 +276,11 @@ class Basis:
 
 def build_steering(mic_xyz, dirs, fs, c, N, materialize_w=False) -> Steering:
     return Steering(mic_xyz, dirs, fs, c, N, materialize_w)
+
+
+def build_steering_nearfield(mic_xyz, src_xyz, fs, c, N, materialize_w=False) -> Steering:
+    """Candidate source positions (metres) instead of directions: Eq. 1."""
+    return Steering(mic_xyz, src_xyz, fs, c, N, materialize_w, nearfield=True)
 
 
 def svd_reduce(steering: Steering, delta: float) -> Basis:

@@ -48,29 +48,34 @@ const char *sp_last_error(void) { return g_err.c_str(); }
 
 int sp_version(void) { return 10000 * 0 + 100 * 1 + 0; }
 
-int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q, double fs,
-                      double c, int N, int flags, sp_steering **out) {
-    SP_CHECK(out != nullptr, SP_EINVAL, "sp_build_steering: out is NULL");
+}  // extern "C"
+
+namespace sp {
+// Offline step 1 for far-field directions (Eq. 2) or near-field source positions (Eq. 1).
+static int build_steering(const char *fn, const double *mic_xyz, int M, const double *dirs, int Q, double fs,
+                          double c, int N, int flags, bool nearfield, sp_steering **out) {
+    const std::string name(fn);
+    SP_CHECK(out != nullptr, SP_EINVAL, name + ": out is NULL");
     *out = nullptr;
-    SP_CHECK(mic_xyz && dirs, SP_EINVAL, "sp_build_steering: null geometry pointer");
-    SP_CHECK(M >= 2 && M <= 64, SP_EINVAL, "sp_build_steering: M must be in [2, 64]");
-    SP_CHECK(Q >= 1 && Q <= (1 << 24), SP_EINVAL, "sp_build_steering: Q must be in [1, 2^24]");
+    SP_CHECK(mic_xyz && dirs, SP_EINVAL, name + ": null geometry pointer");
+    SP_CHECK(M >= 2 && M <= 64, SP_EINVAL, name + ": M must be in [2, 64]");
+    SP_CHECK(Q >= 1 && Q <= (1 << 24), SP_EINVAL, name + ": Q must be in [1, 2^24]");
     SP_CHECK(N >= 4 && N <= 8192 && N % 2 == 0, SP_EINVAL,
-             "sp_build_steering: N must be even and in [4, 8192]");
+             name + ": N must be even and in [4, 8192]");
     SP_CHECK(fs > 0 && c > 0 && std::isfinite(fs) && std::isfinite(c), SP_EINVAL,
-             "sp_build_steering: fs and c must be positive");
-    SP_CHECK((flags & ~SP_STEER_MATERIALIZE_W) == 0, SP_EINVAL, "sp_build_steering: bad flags");
+             name + ": fs and c must be positive");
+    SP_CHECK((flags & ~SP_STEER_MATERIALIZE_W) == 0, SP_EINVAL, name + ": bad flags");
     for (int i = 0; i < 3 * M; ++i)
-        SP_CHECK(std::isfinite(mic_xyz[i]), SP_EINVAL, "sp_build_steering: non-finite mic position");
+        SP_CHECK(std::isfinite(mic_xyz[i]), SP_EINVAL, name + ": non-finite mic position");
     for (int q = 0; q < Q; ++q) {
         const double *s = dirs + 3 * q;
         SP_CHECK(std::isfinite(s[0]) && std::isfinite(s[1]) && std::isfinite(s[2]), SP_EINVAL,
-                 "sp_build_steering: non-finite direction");
+                 name + ": non-finite direction");
         SP_CHECK(s[0] != 0 || s[1] != 0 || s[2] != 0, SP_EINVAL,
-                 "sp_build_steering: zero direction vector");
+                 name + (nearfield ? ": source at the coordinate origin" : ": zero direction vector"));
     }
     sp_steering *st = new (std::nothrow) sp_steering();
-    SP_CHECK(st != nullptr, SP_ENOMEM, "sp_build_steering: host allocation failed");
+    SP_CHECK(st != nullptr, SP_ENOMEM, name + ": host allocation failed");
     cudaGetDevice(&st->device);
     st->M = M;
     st->P = M * (M - 1) / 2;
@@ -82,6 +87,7 @@ int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q, d
     st->c = c;
     st->mic.assign(mic_xyz, mic_xyz + 3 * M);
     st->dirs.assign(dirs, dirs + 3 * (size_t)Q);
+    st->nearfield = nearfield;
     for (int i = 0; i < M; ++i)
         for (int j = i + 1; j < M; ++j) {
             st->pair_i.push_back(i);
@@ -105,6 +111,25 @@ int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q, d
         return rc;
     }
     *out = st;
+    return SP_OK;
+}
+}  // namespace sp
+
+extern "C" {
+
+int sp_build_steering(const double *mic_xyz, int M, const double *dirs, int Q, double fs, double c, int N,
+                      int flags, sp_steering **out) {
+    return build_steering("sp_build_steering", mic_xyz, M, dirs, Q, fs, c, N, flags, false, out);
+}
+
+int sp_build_steering_nearfield(const double *mic_xyz, int M, const double *src_xyz, int Q, double fs, double c,
+                                int N, int flags, sp_steering **out) {
+    return build_steering("sp_build_steering_nearfield", mic_xyz, M, src_xyz, Q, fs, c, N, flags, true, out);
+}
+
+int sp_steering_nearfield(const sp_steering *st, int *nearfield) {
+    SP_CHECK(st && nearfield, SP_EINVAL, "sp_steering_nearfield: null pointer");
+    *nearfield = st->nearfield ? 1 : 0;
     return SP_OK;
 }
 

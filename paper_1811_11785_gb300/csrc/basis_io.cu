@@ -6,11 +6,11 @@
 //   0   char[8]  magic "SVDPHAT1"
 //   8   uint32   version (1)
 //   12  uint32   header bytes (80)
-//   16  int32    M, Q, N, K, n_sigma, reserved (0)
+//   16  int32    M, Q, N, K, n_sigma, model (0: directions, Eq. 2; 1: source positions, Eq. 1)
 //   40  double   fs, c, delta
 //   64  uint64   payload bytes (everything after the header, before the checksum)
 //   72  uint64   reserved (0)
-//   80  double   mic [M][3], dirs [Q][3], sigma2 [n_sigma],
+//   80  double   mic [M][3], dirs (or source positions) [Q][3], sigma2 [n_sigma],
 //                V [L][K] complex (re, im), D [Q][K] complex (re, im)
 //   end uint64   FNV-1a 64 of every preceding byte
 // The device copies (FP32 / FP16 / BF16 operands, direction classes, k-d tree) are rebuilt
@@ -38,7 +38,7 @@ constexpr uint32_t kHeaderBytes = 80;
 struct FileHeader {
     char magic[8];
     uint32_t version, header_bytes;
-    int32_t M, Q, N, K, n_sigma, reserved0;
+    int32_t M, Q, N, K, n_sigma, model;
     double fs, c, delta;
     uint64_t payload_bytes, reserved1;
 };
@@ -76,6 +76,7 @@ extern "C" int sp_save_basis(const sp_basis *b, const char *path) {
     h.N = st->N;
     h.K = b->K;
     h.n_sigma = (int32_t)b->sigma2.size();
+    h.model = st->nearfield ? 1 : 0;
     h.fs = st->fs;
     h.c = st->c;
     h.delta = b->delta;
@@ -123,6 +124,7 @@ extern "C" int sp_load_basis(const char *path, int flags, sp_basis **out, int *K
              "sp_load_basis: unsupported version");
     SP_CHECK(h.M >= 2 && h.M <= 64 && h.Q >= 1 && h.Q <= (1 << 24) && h.N >= 4 && h.N <= 8192 && h.N % 2 == 0,
              SP_EINVAL, "sp_load_basis: geometry out of range");
+    SP_CHECK(h.model == 0 || h.model == 1, SP_EINVAL, "sp_load_basis: unknown steering model");
     const long long L = (long long)h.M * (h.M - 1) / 2 * (h.N / 2 + 1);
     const long long kmax = std::min<long long>(h.Q, L);
     SP_CHECK(h.K >= 1 && h.K <= kmax && h.n_sigma >= h.K && h.n_sigma <= kmax, SP_EINVAL,
@@ -144,7 +146,10 @@ extern "C" int sp_load_basis(const char *path, int flags, sp_basis **out, int *K
     const double *D = V + 2 * (size_t)L * h.K;
 
     sp_steering *st = nullptr;
-    SP_TRY(sp_build_steering(mic, h.M, dirs, h.Q, h.fs, h.c, h.N, flags, &st));
+    if (h.model == 1)
+        SP_TRY(sp_build_steering_nearfield(mic, h.M, dirs, h.Q, h.fs, h.c, h.N, flags, &st));
+    else
+        SP_TRY(sp_build_steering(mic, h.M, dirs, h.Q, h.fs, h.c, h.N, flags, &st));
     sp_basis *b = new (std::nothrow) sp_basis();
     if (!b) {
         sp_steering_destroy(st);

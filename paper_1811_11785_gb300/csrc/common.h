@@ -101,6 +101,7 @@ struct sp_steering {
     int M = 0, P = 0, Q = 0, N = 0, B = 0, L = 0;
     double fs = 0, c = 0;
     std::vector<double> mic, dirs;      // host copies (M x 3, Q x 3)
+    bool nearfield = false;             // dirs are source positions and tau follows Eq. 1
     std::vector<int> pair_i, pair_j;    // Eq. 7 pair order
     std::vector<double> tau_host;       // Q x P
     // Directions whose TDOA vectors agree within 1e-9 samples have identical rows of W

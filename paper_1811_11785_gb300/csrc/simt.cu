@@ -344,18 +344,18 @@ int launch_project_f32(const sp_basis *b, const void *X, int T, void *Z, cudaStr
 
 // ------------------------------------------------------------------------- online step 4
 // Y_qbar = Re{W_qbar X} (Algorithm 1, online step 4).  Because tau_{q,i,j} = d_j - d_i with
-// d_m = fs/c r_m . u_q, every term factors as W_ij X_ij = y_i conj(y_j) with
-// y_m[k] = x^_m[k] exp(-2 pi i k d_m / N), so
+// d_m = fs/c r_m . u_q (Eq. 2; -fs/c ||s_q - r_m|| for Eq. 1), every term factors as
+// W_ij X_ij = y_i conj(y_j) with y_m[k] = x^_m[k] exp(-2 pi i k d_m / N), so
 //     sum_{i<j} Re{y_i conj(y_j)} = (|sum_m y_m|^2 - sum_m |y_m|^2) / 2
 // per bin: O(M) work per bin instead of O(P).  One warp per frame, lane l takes bins
 // l, l + 32, ...; the phasor of mic m at bin k is advanced by exp(-2 pi i 32 d_m / N) from
-// one bin of the lane to the next.  Lane m forms d_m in FP64 (d_m / N split into two floats
-// so that k d_m / N is exact to ~1e-9 turns) and the 32-bin step phasor; both are broadcast.
+// one bin of the lane to the next.  Lane m reads d_m / N (two floats, from FP64, so that
+// k d_m / N is exact to ~1e-9 turns) from the per-direction table built with the steering
+// matrix, forms the 32-bin step phasor and broadcasts both.
 // MMAX: bound on the microphone count (EXACT: M == MMAX at compile time).
 template <int MMAX, bool EXACT>
 __global__ void __launch_bounds__(256)
-    score_row_kernel(const float2 *__restrict__ frames, int T, int M_rt, int B, double inv_n,
-                     const double *__restrict__ unit, const double *__restrict__ mic, double g,
+    score_row_kernel(const float2 *__restrict__ frames, int T, int M_rt, int B, const float4 *__restrict__ tab,
                      const int32_t *__restrict__ idx, float *__restrict__ score) {
     const int M = EXACT ? MMAX : M_rt;
     const int lane = threadIdx.x & 31;
@@ -368,11 +368,9 @@ __global__ void __launch_bounds__(256)
     }
     float my_hi = 0.f, my_lo = 0.f, my_sc = 1.f, my_ss = 0.f;
     if (lane < M) {
-        const double d = g * ((mic[3 * lane] * unit[3 * q] + mic[3 * lane + 1] * unit[3 * q + 1]) +
-                              mic[3 * lane + 2] * unit[3 * q + 2]);
-        const double e = d * inv_n;
-        my_hi = (float)e;
-        my_lo = (float)(e - (double)my_hi);
+        const float4 e = __ldg(tab + (size_t)q * M + lane);
+        my_hi = e.x;
+        my_lo = e.y;
         const float p1 = 32.f * my_hi;
         const float r1 = (p1 - rintf(p1)) + 32.f * my_lo;
         sincospif(-2.f * r1, &my_ss, &my_sc);
@@ -439,8 +437,8 @@ int launch_score_row(const sp_steering *st, const void *frames, int T, const int
     }
     const long long blocks = ((long long)T + 7) / 8;
     auto kern = st->M == 7 ? score_row_kernel<7, true> : st->M <= 8 ? score_row_kernel<8, false> : score_row_kernel<16, false>;
-    kern<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, 1.0 / (double)st->N,
-                                          st->d_dirs.as<double>(), st->d_mic.as<double>(), st->fs / st->c, idx, score);
+    kern<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, st->step4_tab.as<float4>(), idx,
+                                          score);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

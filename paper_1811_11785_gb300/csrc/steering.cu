@@ -1,5 +1,5 @@
-// Offline step 1 of Algorithm 1: the far-field TDOA table (Eq. 2) and the steering
-// matrix W (Eq. 4, stacked as Eq. 8).
+// Offline step 1 of Algorithm 1: the TDOA table (Eq. 2 in the far field, Eq. 1 for sources
+// at given positions) and the steering matrix W (Eq. 4, stacked as Eq. 8).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,14 +10,22 @@
 
 namespace sp {
 
-// tau[q][p] = fs/c * (r_j - r_i) . s_q / ||s_q||  (Eq. 2), one thread per (q, p).
+// ||s - r|| in the fixed order sqrt((ex*ex + ey*ey) + ez*ez), e = s - r.
+__device__ __forceinline__ double dist_rn(double sx, double sy, double sz, const double *r) {
+    const double ex = __dsub_rn(sx, r[0]), ey = __dsub_rn(sy, r[1]), ez = __dsub_rn(sz, r[2]);
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+}
+
+// Far field (Eq. 2): tau[q][p] = fs/c * (r_j - r_i) . s_q / ||s_q||, one thread per (q, p).
 // Fixed order, every operation correctly rounded and never contracted into an FMA:
 //   n = sqrt((sx*sx + sy*sy) + sz*sz), u = s / n,
 //   tau = (fs / c) * ((dx*ux + dy*uy) + dz*uz), d = r_j - r_i.
-// The same order on any IEEE-754 machine gives the same bits.
+// Near field (Eq. 1, s_q a source position): tau = (fs / c) * (||s_q - r_i|| - ||s_q - r_j||)
+// with each norm in the order of dist_rn.  The same order on any IEEE-754 machine gives the
+// same bits.  unit[q] = s_q / ||s_q|| in both cases.
 __global__ void tau_kernel(const double *__restrict__ mic, const double *__restrict__ dirs,
                            const int *__restrict__ pi, const int *__restrict__ pj, int Q, int P,
-                           double fs, double c, double *__restrict__ tau, double *__restrict__ unit) {
+                           double fs, double c, int nearfield, double *__restrict__ tau, double *__restrict__ unit) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)Q * P) return;
     const int q = (int)(idx / P), p = (int)(idx % P);
@@ -26,12 +34,16 @@ __global__ void tau_kernel(const double *__restrict__ mic, const double *__restr
                                           __dmul_rn(sz, sz)));
     const double ux = __ddiv_rn(sx, n), uy = __ddiv_rn(sy, n), uz = __ddiv_rn(sz, n);
     const int i = pi[p], j = pj[p];
-    const double dx = __dsub_rn(mic[3 * j], mic[3 * i]);
-    const double dy = __dsub_rn(mic[3 * j + 1], mic[3 * i + 1]);
-    const double dz = __dsub_rn(mic[3 * j + 2], mic[3 * i + 2]);
     const double g = __ddiv_rn(fs, c);
-    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(dx, ux), __dmul_rn(dy, uy)), __dmul_rn(dz, uz));
-    tau[idx] = __dmul_rn(g, dot);
+    if (nearfield) {
+        tau[idx] = __dmul_rn(g, __dsub_rn(dist_rn(sx, sy, sz, mic + 3 * i), dist_rn(sx, sy, sz, mic + 3 * j)));
+    } else {
+        const double dx = __dsub_rn(mic[3 * j], mic[3 * i]);
+        const double dy = __dsub_rn(mic[3 * j + 1], mic[3 * i + 1]);
+        const double dz = __dsub_rn(mic[3 * j + 2], mic[3 * i + 2]);
+        const double dot = __dadd_rn(__dadd_rn(__dmul_rn(dx, ux), __dmul_rn(dy, uy)), __dmul_rn(dz, uz));
+        tau[idx] = __dmul_rn(g, dot);
+    }
     if (p == 0) {
         unit[3 * q] = ux;
         unit[3 * q + 1] = uy;
@@ -57,14 +69,19 @@ __global__ void w_kernel(const double *__restrict__ tau, int Q, int P, int B, in
 }
 
 // Per direction q and microphone m, for online step 4: d_m / N in turns per bin, split as
-// float hi + lo (d_m = fs/c r_m . u_q in FP64), and the phasor exp(-2 pi i 64 d_m / N) of a
-// 64-bin step.  Computed once here so that the step-4 kernel does no FP64 work per frame.
-__global__ void step4_table_kernel(const double *__restrict__ mic, const double *__restrict__ unit, int Q, int M,
-                                   double g, double inv_n, float4 *__restrict__ tab) {
+// float hi + lo, and the phasor exp(-2 pi i 64 d_m / N) of a 64-bin step, where
+// tau_{q,i,j} = d_j - d_i: d_m = fs/c r_m . u_q in the far field (Eq. 2) and
+// d_m = -fs/c ||s_q - r_m|| in the near field (Eq. 1), in FP64.  Computed once here so that
+// the step-4 kernel does no FP64 work per frame.
+__global__ void step4_table_kernel(const double *__restrict__ mic, const double *__restrict__ unit,
+                                   const double *__restrict__ pos, int nearfield, int Q, int M, double g,
+                                   double inv_n, float4 *__restrict__ tab) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)Q * M) return;
     const int q = (int)(idx / M), m = (int)(idx % M);
-    const double d = g * ((mic[3 * m] * unit[3 * q] + mic[3 * m + 1] * unit[3 * q + 1]) + mic[3 * m + 2] * unit[3 * q + 2]);
+    const double d =
+        nearfield ? -g * dist_rn(pos[3 * q], pos[3 * q + 1], pos[3 * q + 2], mic + 3 * m)
+                  : g * ((mic[3 * m] * unit[3 * q] + mic[3 * m + 1] * unit[3 * q + 1]) + mic[3 * m + 2] * unit[3 * q + 2]);
     const double e = d * inv_n;
     const float hi = (float)e;
     const float lo = (float)(e - (double)hi);
@@ -90,14 +107,14 @@ int launch_tau(const sp_steering *st, cudaStream_t s) {
     const long long n = (long long)st->Q * st->P;
     tau_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
         m->d_mic.as<double>(), d_dirs_in.as<double>(), d_pairs.as<int>(), d_pairs.as<int>() + st->P,
-        st->Q, st->P, st->fs, st->c, m->tau.as<double>(), m->d_dirs.as<double>());
+        st->Q, st->P, st->fs, st->c, st->nearfield ? 1 : 0, m->tau.as<double>(), m->d_dirs.as<double>());
     SP_CUDA(cudaGetLastError());
     {
         const long long nm = (long long)st->Q * st->M;
         SP_TRY(m->step4_tab.reserve((size_t)nm * 16));
         step4_table_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(
-            m->d_mic.as<double>(), m->d_dirs.as<double>(), st->Q, st->M, st->fs / st->c, 1.0 / (double)st->N,
-            m->step4_tab.as<float4>());
+            m->d_mic.as<double>(), m->d_dirs.as<double>(), d_dirs_in.as<double>(), st->nearfield ? 1 : 0, st->Q,
+            st->M, st->fs / st->c, 1.0 / (double)st->N, m->step4_tab.as<float4>());
         SP_CUDA(cudaGetLastError());
     }
     SP_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed on return

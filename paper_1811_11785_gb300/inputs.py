@@ -233,6 +233,34 @@ def plane_wave_frames(
     return out
 
 
+def spherical_wave_frames(rng: np.random.Generator, mic_xyz: np.ndarray, N: int, fs: float, c: float,
+                          src_xyz: np.ndarray, snr_db: np.ndarray, dtype=np.complex64) -> np.ndarray:
+    """STFT frames ``[T][M][N/2+1]`` of one white point source per frame at position
+    ``src_xyz[t]`` (metres) plus independent white noise per microphone: microphone m
+    receives the source delayed by its distance, ``fs/c * ||s - r_m||`` samples, applied as
+    a phase ramp in frequency.  SNR as in ``plane_wave_frames``."""
+    mic_xyz = np.asarray(mic_xyz, dtype=np.float64)
+    src_xyz = np.asarray(src_xyz, dtype=np.float64)
+    T, M, B = src_xyz.shape[0], mic_xyz.shape[0], N // 2 + 1
+    win = hann(N)
+    k = np.arange(B, dtype=np.float64)
+    spec = _windowed_spectra(rng, (T, 1), N, win)[:, 0, :]                          # (T, B)
+    dist = np.sqrt(((src_xyz[:, None, :] - mic_xyz[None, :, :]) ** 2).sum(-1))       # (T, M)
+    sig = spec[:, None, :] * np.exp(-2j * np.pi * (fs / c) * dist[:, :, None] * k[None, None, :] / N)
+    nz = _windowed_spectra(rng, (T, M), N, win)
+    ps = np.mean(np.abs(sig) ** 2, axis=(1, 2))
+    pn = np.mean(np.abs(nz) ** 2, axis=(1, 2))
+    g = np.sqrt(ps / (pn * 10.0 ** (np.asarray(snr_db, dtype=np.float64) / 10.0)))
+    return (sig + g[:, None, None] * nz).astype(dtype)
+
+
+def nearfield_points(level: int = 2, radii=(0.25, 0.5, 1.0)) -> np.ndarray:
+    """Candidate source positions for the near-field steering (Eq. 1): the level-``level``
+    icosphere directions at each radius (metres), radius-major."""
+    u = icosphere(level)
+    return np.concatenate([r * u for r in radii], axis=0)
+
+
 # --------------------------------------------------------------------------------------
 # Workload presets (the five configurations the build is measured on)
 # --------------------------------------------------------------------------------------

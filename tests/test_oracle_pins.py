@@ -50,6 +50,32 @@ def test_tdoa_hand_value():
     assert tau[:, 0] == pytest.approx([8.0, 0.0, -8.0], abs=1e-12)
 
 
+def test_nearfield_tdoa_hand_values_eq1():
+    """Eq. 1 by hand: two mics 8c/fs apart on x; a source on the axis beyond mic 1 is
+    8 samples closer to it (tau = +8), beyond mic 0 the opposite (-8), on the perpendicular
+    bisector 0; a source sitting on mic 0 gives -(fs/c) * ||r_1 - r_0|| = -8."""
+    c, fs = 343.0, 16000.0
+    a = 8 * c / fs
+    mic = np.array([[0.0, 0, 0], [a, 0, 0]])
+    src = np.array([[2.0, 0, 0], [-2.0, 0, 0], [a / 2, 1.3, -0.4], [0.0, 0, 0]])
+    tau = O.tdoa_nearfield(mic, src, fs, c)
+    assert tau[:, 0] == pytest.approx([8.0, -8.0, 0.0, -8.0], abs=1e-9)
+
+
+def test_nearfield_tdoa_is_a_difference_of_distances():
+    """Eq. 1 for every pair is d_j - d_i with d_m = -fs/c ||s - r_m||, so around any mic
+    triangle the TDOAs close: tau_ij + tau_jk = tau_ik; and swapping a pair negates it."""
+    rng = np.random.default_rng(3)
+    mic = I.array_random_ball(rng, 6)
+    src = rng.normal(size=(40, 3)) * 0.7
+    tau = O.tdoa_nearfield(mic, src, 16000.0, 343.0)
+    P = {pq: p for p, pq in enumerate(O.pairs(6))}
+    for (i, j, k) in [(0, 1, 2), (1, 3, 5), (0, 2, 4), (2, 4, 5)]:
+        assert np.max(np.abs(tau[:, P[(i, j)]] + tau[:, P[(j, k)]] - tau[:, P[(i, k)]])) < 1e-11
+    flipped = O.tdoa_nearfield(mic[::-1], src, 16000.0, 343.0)
+    assert np.max(np.abs(flipped[:, P[(0, 5)]] + tau[:, P[(0, 5)]])) < 1e-11   # pair (5, 0) reversed
+
+
 def test_dirs_need_not_be_unit():
     mic = I.array_planar_2d_circle()
     u = I.icosphere(2)
