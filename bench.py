@@ -5,15 +5,19 @@ B = 257 bins), Q = 2562 icosphere directions, K from delta = 1e-5 (K = 48), 65,5
 per step with one white-noise plane-wave source per frame at SNR U(-5, 20) dB (synthetic).
 A step is one pass of Algorithm 1's online path over the batch: PHAT -> Z = V^H X ->
 exhaustive Re{D Z} argmax (FP16 tensor cores, then FP32 rescoring of every class within the
-FP16 rounding bound of the best) -> Y_qbar from the row of W (online step 4): three kernel
-launches.  The STFT batch (943 MB) is larger than L2, so no flush is needed.
+FP16 rounding bound of the best; frames with more than 16 such classes go to an FP32 scan
+over every class on a device list, empty on this workload) -> Y_qbar from the row of W
+(online step 4): five kernel launches (GEMM1, scan, list scan, list finalize, step 4) and a
+4-byte reset of the list count.  The STFT batch (943 MB) is larger than L2, so no flush is
+needed.
 
 Extra keys (unless --no-extras): the same frames through FP32 SRP-PHAT, the FP32 / BF16
 paths and the k-d tree; the 3-D 7-mic array with Q = 10242 (exhaustive, learned proposal,
-k-d tree on 2^20 frames); 256 batched streams in one CUDA-graph launch.
+k-d tree on 2^20 frames); 256 batched streams in one CUDA-graph launch.  --only c5 (opt-in,
+minutes of basis set-up): the 16-mic, N = 1024 array on the level-6 grid (Q = 40,962).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec fp16|bf16]
-                [--frames T] [--no-extras] [--only array3d|batched] [--array3d-frames T]
+                [--frames T] [--no-extras] [--only array3d|batched|c5] [--array3d-frames T]
 Under torchrun each rank localises its own 65,536 frames (weak scaling, no collective on the
 data path); rank 0 prints one JSON line.
 """
@@ -559,7 +563,7 @@ def main():
             "config": arm_config(b.K, T),
             "agreement_vs_oracle": agree, "agreement_sample_frames": int(len(sel)),
             "score_error_vs_oracle": {"search_score_max_over_L": proj_err, "step4_score_max_over_L": s4_err},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 5 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": TRAFFIC_PER_FRAME and TRAFFIC_PER_FRAME * T,
                          "kernel": "svd_proj_kernel", "kernel_ms": k_ms, "peak_source": peak_kind,
