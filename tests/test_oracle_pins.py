@@ -204,6 +204,29 @@ def test_noiseless_plane_wave_localises_to_grid_point_eq2_to_eq6(arr, lvl):
         assert np.all(best <= L * (1 + 1e-12))
 
 
+def test_noiseless_spherical_wave_localises_to_its_position_eq1():
+    """A noiseless point source at candidate position q0 delays microphone m by
+    fs/c ||s - r_m|| samples; with the Eq. 1 table its PHAT cross spectra are conj(W_q0), so
+    Y_q0 = L and q0's class is the SRP-PHAT argmax (this fixes the generator's sign against
+    Eq. 1 and Eq. 4).  The same direction at another radius is a different point."""
+    mic = I.array_3d()
+    pts = I.nearfield_points(1, radii=(0.3, 0.6, 1.2))          # 126 positions
+    fs, c, N = 16000.0, 343.0, 128
+    tau = O.tdoa_nearfield(mic, pts, fs, c)
+    W = O.steering(tau, N)
+    cls = O.direction_classes(tau)
+    L = W.shape[1]
+    for q0 in [0, 40, 77, 125]:
+        src = np.repeat(pts[q0][None, :], 2, axis=0)
+        fr = I.spherical_wave_frames(np.random.default_rng(q0), mic, N, fs, c, src, np.full(2, 400.0),
+                                     dtype=np.complex128)
+        Y = O.srp_scores(W, O.phat(fr))
+        idx, best = O.argmax_lowest(Y)
+        assert np.all(idx == q0) and np.all(cls[idx] == q0)
+        assert Y[0, q0] == pytest.approx(L, rel=1e-9)
+        assert np.all(best <= L * (1 + 1e-12))
+
+
 # ---------------------------------------------------------------------------- eigen / SVD
 
 def test_jacobi_2x2_closed_form():
