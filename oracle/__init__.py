@@ -24,6 +24,8 @@ Readings of the paper (where it is silent, garbled or inconsistent):
 * A spectrum entry whose squared magnitude is below 1e-30 is "zero" and every cross
   spectrum that uses it is 0 (Eq. 3 divides by the magnitudes).
 * Ties in an argmax go to the lowest index.
+* Eq. 1 (near field) takes ``s_q`` as a candidate source position in the microphones'
+  frame; Eq. 2 is its limit for a distant source (Section 2), pinned as such.
 """
 from __future__ import annotations
 
