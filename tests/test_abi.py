@@ -44,23 +44,41 @@ def test_version_and_error_string(lib):
     assert isinstance(lib.sp_last_error(), bytes)
 
 
-def _bs(lib, M=3, Q=4, N=16, fs=16000.0, c=343.0, flags=0, null_out=False, zero_dir=False):
+def _bs(lib, M=3, Q=4, N=16, fs=16000.0, c=343.0, flags=0, null_out=False, zero_dir=False, nan_dir=False,
+        near=False):
     mic = np.zeros((M, 3))
     mic[:, 0] = np.arange(M) * 0.01
     d = np.tile([0.0, 0.0, 1.0], (max(Q, 1), 1))
     if zero_dir:
         d[0] = 0.0
+    if nan_dir:
+        d[0, 1] = np.nan
     h = ctypes.c_void_p()
     dp = ctypes.POINTER(ctypes.c_double)
-    return lib.sp_build_steering(mic.ctypes.data_as(dp), M, d.ctypes.data_as(dp), Q, fs, c, N, flags,
-                                 None if null_out else ctypes.byref(h))
+    fn = lib.sp_build_steering_nearfield if near else lib.sp_build_steering
+    return fn(mic.ctypes.data_as(dp), M, d.ctypes.data_as(dp), Q, fs, c, N, flags,
+              None if null_out else ctypes.byref(h))
 
 
-@pytest.mark.parametrize("kw", [dict(M=1), dict(M=65), dict(Q=0), dict(N=15), dict(N=2), dict(fs=0.0),
-                                dict(c=-1.0), dict(flags=8), dict(null_out=True), dict(zero_dir=True)])
-def test_build_steering_rejects_bad_arguments(lib, kw):
-    assert _bs(lib, **kw) == api.SP_EINVAL
-    assert len(lib.sp_last_error()) > 0
+BAD_STEERING = [dict(M=1), dict(M=65), dict(Q=0), dict(N=15), dict(N=2), dict(fs=0.0), dict(c=-1.0), dict(flags=8),
+                dict(null_out=True), dict(zero_dir=True), dict(nan_dir=True)]
+
+
+@pytest.mark.parametrize("near", [False, True])
+@pytest.mark.parametrize("kw", BAD_STEERING)
+def test_build_steering_rejects_bad_arguments(lib, kw, near):
+    """Both builders (directions, Eq. 2; source positions, Eq. 1) refuse bad geometry with
+    SP_EINVAL on the host, naming themselves in the message."""
+    assert _bs(lib, near=near, **kw) == api.SP_EINVAL
+    msg = lib.sp_last_error()
+    assert msg.startswith(b"sp_build_steering_nearfield" if near else b"sp_build_steering:")
+    if kw.get("zero_dir"):
+        assert (b"origin" in msg) if near else (b"zero direction" in msg)
+
+
+def test_steering_model_query_rejects_null(lib):
+    nf = ctypes.c_int()
+    assert lib.sp_steering_nearfield(None, ctypes.byref(nf)) == api.SP_EINVAL
 
 
 def test_other_entry_points_reject_null_handles(lib):
