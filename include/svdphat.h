@@ -258,12 +258,17 @@ int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode 
  * idx_dev, score_dev, proj_score_dev: as for sp_localize.  The caller still provides the
  * frames and all outputs.
  *
- * The first call on a device looks up the array's device address (with that device
- * current) and caches it; make that first call before any stream capture.  The call itself
- * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).  Every call
- * on a device shares the one array, which keeps the last call's contents; nothing in it
- * needs to start at zero.  Calls whose work overlaps on the GPU (other streams, other
- * threads) race on the array: serialise them. */
+ * Arguments are checked as in sp_localize (SP_EINVAL for a NULL or misaligned pointer, T < 0
+ * or T > 2^28), and a basis without a tensor-core plan (2K > 320) gives SP_ENOTIMPL.
+ *
+ * Warm-up: the first call on a device looks up the array's device address (with that
+ * device current) and caches it, and the first launch of each kernel loads it and sets its
+ * shared-memory limit.  A call with T == 0 does all of this and launches nothing: make one
+ * such call per device and basis, outside the processing path and before any stream
+ * capture.  After it, calls allocate nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  Every call on a device shares the one array, which keeps the last
+ * call's contents; nothing in it needs to start at zero.  Calls whose work overlaps on the
+ * GPU (other streams, other threads) race on the array: serialise them. */
 int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
                         int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream);
 
@@ -287,8 +292,9 @@ int sp_set_wait_budget(long long iterations);
  * complex64, the caller's buffer, read at every run), T[i] >= 1, mode and prec as in
  * sp_localize, idx_dev[i] / score_dev[i] / proj_dev[i] as in sp_localize (score_dev and
  * proj_dev may be NULL arrays or hold NULL entries).  Shapes and pointers are fixed for the
- * plan's lifetime.  Synchronous: it runs every stream once (sizing the workspaces), then
- * captures the graph; with SP_BATCH_AUTOTUNE it builds and times the candidate launch
+ * plan's lifetime.  Synchronous: after the work already queued on `stream` (which may be
+ * writing the frames), it runs every stream once (sizing the workspaces), then captures the
+ * graph; with SP_BATCH_AUTOTUNE it builds and times the candidate launch
  * shapes (branches in {8, 32, 128, n} x tiles per GEMM1 CTA in {1, 2, 4}) and keeps the
  * fastest.  Errors: SP_EINVAL (bad arguments, per stream as sp_localize), SP_ECUDA.
  * sp_batch_run: one graph launch on stream (asynchronous).

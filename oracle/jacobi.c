@@ -15,7 +15,8 @@
  * sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c).  A <- U^H A U, V <- V U.
  * Sweeps run row by row over all p < q until off(A) <= tol * ||A||_F.
  *
- * Storage: row-major n x n, real and imaginary parts in separate arrays.
+ * Storage: row-major n x n, real and imaginary parts in separate arrays.  The
+ * eigenvectors come back transposed: row p of (Vr, Vi) is the eigenvector of A[p][p].
  * Compiled with -O2 -ffp-contract=off (no fused multiply-add contraction).
  */
 #include <math.h>
@@ -86,15 +87,16 @@ int oracle_jacobi_herm(int n, double *Ar, double *Ai, double *Vr, double *Vi,
                 Ar[q * n + p] = Ai[q * n + p] = 0.0;
                 Ai[p * n + p] = Ai[q * n + q] = 0.0;
 
-                /* eigenvectors: V <- V U (same column rule as A) */
+                /* eigenvectors: V <- V U (same column rule as A); V is held transposed
+                 * (row p of Vt is column p of V) so that this update runs along rows */
                 for (k = 0; k < n; ++k) {
-                    double xr = Vr[k * n + p], xi = Vi[k * n + p];
-                    double yr = Vr[k * n + q], yi = Vi[k * n + q];
+                    double xr = Vr[p * n + k], xi = Vi[p * n + k];
+                    double yr = Vr[q * n + k], yi = Vi[q * n + k];
                     double zr = er * yr + ei * yi, zi = er * yi - ei * yr;
-                    Vr[k * n + p] = c * xr - s * zr;
-                    Vi[k * n + p] = c * xi - s * zi;
-                    Vr[k * n + q] = s * xr + c * zr;
-                    Vi[k * n + q] = s * xi + c * zi;
+                    Vr[p * n + k] = c * xr - s * zr;
+                    Vi[p * n + k] = c * xi - s * zi;
+                    Vr[q * n + k] = s * xr + c * zr;
+                    Vi[q * n + k] = s * xi + c * zi;
                 }
             }
         }

@@ -6,8 +6,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 #include <string>
+#include <utility>
 
 #include "common.h"
 
@@ -37,6 +40,32 @@ int DevBuf::reserve(size_t n) {
 }
 
 static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static std::mutex g_dev_mu;
+
+int num_sms() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+int ensure_max_smem(const void *kernel) {
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    SP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (done.count({dev, kernel})) return SP_OK;
+    SP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+    done.insert({dev, kernel});
+    return SP_OK;
+}
 
 }  // namespace sp
 

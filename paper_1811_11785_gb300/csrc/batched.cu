@@ -155,6 +155,10 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
     }
     SP_CUDA(cudaStreamCreateWithFlags(&bt->origin, cudaStreamNonBlocking));
     SP_CUDA(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+    // the plan's own stream runs after the work already queued on the caller's stream (which
+    // may still be writing the frames, or reading earlier results from the output buffers)
+    SP_CUDA(cudaEventRecord(bt->fork, (cudaStream_t)stream));
+    SP_CUDA(cudaStreamWaitEvent(bt->origin, bt->fork, 0));
     // one eager pass: sizes every workspace (no allocation happens while capturing) and
     // sets the kernels' attributes
     for (int i = 0; i < n; ++i) SP_TRY(enqueue_stream(bt.get(), i, bt->origin, 1));
@@ -191,7 +195,6 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
         bt->tiles_per_cta = 1;
         SP_TRY(build_graph(bt.get(), bt->branches, 1, &bt->exec));
     }
-    (void)stream;
     *out = bt.release();
     return SP_OK;
 }

@@ -187,11 +187,21 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
 int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
                   cudaStream_t s);
 int tc_prepare(sp_basis *b);
+// Load the kernels a localisation of this basis / array would launch on the current device
+// and set their shared-memory limits (what their first launches would otherwise do).
+int prepare_tc(const sp_basis *b, int prec);
+int prepare_simt(const sp_steering *st);
+int prepare_step4(const sp_steering *st);
 // 2-D tensor map of a row-major [rows][inner] fp16 (bf16 = 0) / bf16 (bf16 = 1) array,
 // 128-byte swizzle, box {box_inner, box_rows}
 int encode_tmap_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint64_t rows, uint32_t box_inner,
                    uint32_t box_rows);
-int num_sms();   // upload GEMM1/GEMM2 operands in the tensor-core layouts
+// Multiprocessor count of the current device (looked up once per device).
+int num_sms();
+// Raise a kernel's dynamic shared-memory limit to 227 KB on the current device.  The
+// attribute belongs to the device, so it is set once per (device, kernel) pair; a process
+// that drives several GPUs sets it on each.  Thread-safe.
+int ensure_max_smem(const void *kernel);
 int reduce_basis(const sp_steering *st, double delta, sp_basis *b);
 int install_basis(sp_basis *b);   // device copies of b->V, b->D (host FP64, filled)
 int build_kdtree(sp_basis *b);

@@ -952,11 +952,7 @@ int launch_mlp(const sp_proposal *p, const void *Z, const float *zn2, int T, flo
     const int n_bias = p->H1 + p->H2 + p->C;
     const int smem = kAAtoms * kAAtomBytes + kWRing * kWAtomBytes + ((n_bias * 4 + 15) / 16) * 16 +
                      (2 * kWRing + 6) * 8 + 16 + 1024;
-    static bool attr = false;
-    if (!attr) {
-        SP_CUDA(cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-        attr = true;
-    }
+    SP_TRY(ensure_max_smem((const void *)mlp_tc_kernel));
     SP_CHECK(smem <= 232448, SP_ENOTIMPL, "proposal: network too large for the shared-memory plan");
     const int grid = std::min(m.n_tiles, num_sms());
     mlp_tc_kernel<<<grid, kMlpThreads, smem, s>>>(p->tm[0], p->tm[1], p->tm[2], m);

@@ -46,15 +46,12 @@ using namespace sp;
 
 extern "C" int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
                                    int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream) {
-    SP_CHECK(b, SP_EINVAL, "sp_localize_noalloc: null basis");
-    SP_CHECK(T >= 0, SP_EINVAL, "sp_localize_noalloc: T < 0");
+    // the same argument checks as sp_localize (frames, T range, output pointers and alignment)
+    SP_TRY(check_localize_args(b, frames_dev, T, idx_dev, score_dev, proj_score_dev));
     SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_ENOTIMPL,
              "sp_localize_noalloc: only SP_PREC_FP16 and SP_PREC_BF16");
-    SP_CHECK(b->st->M <= 16, SP_ENOTIMPL, "sp_localize_noalloc: M <= 16 microphones");
-    if (T == 0) return SP_OK;
-    SP_CHECK(frames_dev && idx_dev, SP_EINVAL, "sp_localize_noalloc: null frames or idx pointer");
-    SP_CHECK(reinterpret_cast<uintptr_t>(frames_dev) % 8 == 0 && reinterpret_cast<uintptr_t>(idx_dev) % 4 == 0,
-             SP_EINVAL, "sp_localize_noalloc: misaligned pointer");
+    SP_CHECK(b->tc.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
+             "sp_localize_noalloc: the tensor-core path supports 2K <= 320 and M <= 16");
     const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
     const size_t nbytes = ((size_t)T * 4 + 255) / 256 * 256;
     const size_t need = zbytes + nbytes + scan_workspace_bytes(T);
@@ -63,6 +60,14 @@ extern "C" int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, in
                  std::to_string(need) + " bytes requested)");
     void *scratch = nullptr;
     SP_TRY(noalloc_scratch(&scratch));
+    if (T == 0) {
+        // the warm-up call: with the scratch address cached above, load every kernel a call on
+        // this basis can launch and set their shared-memory limits, so that later calls do
+        // neither on the caller's processing path
+        SP_TRY(prepare_tc(b, (int)prec));
+        SP_TRY(prepare_simt(b->st));
+        return prepare_step4(b->st);
+    }
     char *z = static_cast<char *>(scratch);
     float *zn2 = reinterpret_cast<float *>(z + zbytes);
     cudaStream_t s = (cudaStream_t)stream;

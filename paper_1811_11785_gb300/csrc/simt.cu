@@ -92,14 +92,23 @@ __global__ void finalize_keys_kernel(const unsigned long long *__restrict__ keys
 // List mode (count != null): the rows of X are list[0 .. *count), read from device memory
 // when the kernel starts, and keys are indexed by list position; CTAs stride over the
 // (q tile, t tile) items, so an empty list costs one read per CTA.
+// Blocked summation (blocked != 0, long contractions such as SRP's 2L = 10,794 terms): each
+// output's register accumulator covers one block of RA_K * kBlockIters complex entries and
+// is then added to a running total in shared memory (64 KB of dynamic shared memory, one
+// column per thread, conflict-free).  The partial sums that round then stay below
+// 2 * 256 in magnitude instead of growing to L, so the FP32 rounding error of a score
+// drops from about u L sqrt(2L) to about u L sqrt(L / 256) (u = 2^-24).
 constexpr int RA_M = 128, RA_N = 128, RA_K = 8;
+constexpr int kBlockIters = 32;                 // 256 complex entries per block
+constexpr int kBlockedSmem = 64 * 256 * 4;      // running totals: 64 outputs x 256 threads
 
 __global__ void __launch_bounds__(256, 2)
     re_argmax_kernel(const float2 *__restrict__ A, int Qa, int Lc, const float2 *__restrict__ X, int T_in,
                      int nq, unsigned long long *__restrict__ keys, const int32_t *__restrict__ list,
-                     const int *__restrict__ count) {
+                     const int *__restrict__ count, int blocked) {
     __shared__ __align__(16) float As[2][2 * RA_K][RA_M + 4];
     __shared__ __align__(16) float Bs[2][2 * RA_K][RA_N + 4];
+    extern __shared__ float tot_s[];   // [64][256] when blocked
     const int tid = threadIdx.x;
     const int T = count ? *count : T_in;
     const long long n_items = (long long)nq * (((long long)T + RA_N - 1) / RA_N);
@@ -139,11 +148,14 @@ __global__ void __launch_bounds__(256, 2)
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        if (blocked)
+#pragma unroll
+            for (int e = 0; e < 64; ++e) tot_s[e * 256 + tid] = 0.f;
 
         gload(0);
         sstore(0);
         __syncthreads();
-        int buf = 0;
+        int buf = 0, it = 0;
         for (int k0 = 0; k0 < Lc; k0 += RA_K) {
             const bool more = k0 + RA_K < Lc;
             if (more) gload(k0 + RA_K);
@@ -169,7 +181,22 @@ __global__ void __launch_bounds__(256, 2)
             if (more) sstore(buf ^ 1);
             __syncthreads();
             buf ^= 1;
+            if (blocked && ++it == kBlockIters) {   // close the block: total += block sum
+                it = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        tot_s[(i * 8 + j) * 256 + tid] += acc[i][j];
+                        acc[i][j] = 0.f;
+                    }
+            }
         }
+        if (blocked)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = tot_s[(i * 8 + j) * 256 + tid] + acc[i][j];
 
         // per-thread best over its 8 q rows (ascending q), for each of its 8 frames
         unsigned long long *red = reinterpret_cast<unsigned long long *>(&As[0][0][0]);  // [16][128]
@@ -223,9 +250,10 @@ static int launch_re_argmax(const void *A, int Qa, int Lc, const void *X, int T,
     SP_CUDA(cudaMemsetAsync(keys, 0, (size_t)T * 8, s));
     const int nq = (Qa + RA_M - 1) / RA_M;
     const long long nt = ((long long)T + RA_N - 1) / RA_N;
-    re_argmax_kernel<<<(unsigned)(nq * nt), 256, 0, s>>>((const float2 *)A, Qa, Lc,
-                                                          (const float2 *)X, T, nq,
-                                                          (unsigned long long *)keys, nullptr, nullptr);
+    const int blocked = Lc > RA_K * kBlockIters ? 1 : 0;
+    if (blocked) SP_TRY(ensure_max_smem((const void *)re_argmax_kernel));
+    re_argmax_kernel<<<(unsigned)(nq * nt), 256, blocked ? kBlockedSmem : 0, s>>>(
+        (const float2 *)A, Qa, Lc, (const float2 *)X, T, nq, (unsigned long long *)keys, nullptr, nullptr, blocked);
     SP_CUDA(cudaGetLastError());
     finalize_keys_kernel<<<(T + 255) / 256, 256, 0, s>>>((const unsigned long long *)keys, T, remap, idx, best);
     SP_CUDA(cudaGetLastError());
@@ -248,7 +276,7 @@ int launch_svd_scan_f32_list(const sp_basis *b, const void *Z, int T_cap, const 
     const long long items = (long long)nq * (((long long)T_cap + RA_N - 1) / RA_N);
     const unsigned grid = (unsigned)std::min<long long>(items, 2LL * num_sms());
     re_argmax_kernel<<<grid, 256, 0, s>>>(b->Dc32r.as<float2>(), Qa, b->K, (const float2 *)Z, T_cap, nq,
-                                          (unsigned long long *)keys, list, count);
+                                          (unsigned long long *)keys, list, count, 0);
     SP_CUDA(cudaGetLastError());
     const unsigned fgrid = (unsigned)std::min<long long>(((long long)T_cap + 255) / 256, num_sms());
     finalize_list_kernel<<<fgrid, 256, 0, s>>>((const unsigned long long *)keys, count, list,
@@ -440,6 +468,19 @@ int launch_score_row(const sp_steering *st, const void *frames, int T, const int
     kern<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)frames, T, st->M, st->B, st->step4_tab.as<float4>(), idx,
                                           score);
     SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+// Loads the list-scan kernels and the warp-per-frame step-4 kernel for this array on the
+// current device (what their first launches would otherwise do).
+int prepare_simt(const sp_steering *st) {
+    cudaFuncAttributes a;
+    SP_CUDA(cudaFuncGetAttributes(&a, (const void *)re_argmax_kernel));
+    SP_CUDA(cudaFuncGetAttributes(&a, (const void *)finalize_list_kernel));
+    if (st->M <= 16) {
+        auto kern = st->M == 7 ? score_row_kernel<7, true> : st->M <= 8 ? score_row_kernel<8, false> : score_row_kernel<16, false>;
+        SP_CUDA(cudaFuncGetAttributes(&a, (const void *)kern));
+    }
     return SP_OK;
 }
 

@@ -213,16 +213,24 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
     const int smem = (int)(p.n_slots * slot_bytes + 2 * kMaxSlots * 8 + 4 * kTeams * 4 + 16 + 128);
     auto kern = st->M == 7 ? step4_bulk_kernel<7, true>
                            : st->M <= 8 ? step4_bulk_kernel<8, false> : step4_bulk_kernel<16, false>;
-    const int which = st->M == 7 ? 0 : st->M <= 8 ? 1 : 2;
-    static bool attr[3] = {false, false, false};
-    if (!attr[which]) {
-        SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-        attr[which] = true;
-    }
+    SP_TRY(ensure_max_smem((const void *)kern));
     const int grid = std::min(p.n_pairs, num_sms());
     kern<<<grid, kThreads, smem, s>>>(p);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
+}
+
+// Loads the bulk-copy step-4 kernel for this array on the current device and raises its
+// shared-memory limit (what the first launch would otherwise do).
+int prepare_step4(const sp_steering *st) {
+    int *status = nullptr;
+    SP_TRY(device_status_ptr(&status));   // the status word's address, cached per device
+    if (st->M > 16) return SP_OK;
+    auto kern = st->M == 7 ? step4_bulk_kernel<7, true>
+                           : st->M <= 8 ? step4_bulk_kernel<8, false> : step4_bulk_kernel<16, false>;
+    cudaFuncAttributes a;
+    SP_CUDA(cudaFuncGetAttributes(&a, (const void *)kern));
+    return ensure_max_smem((const void *)kern);
 }
 
 }  // namespace sp

@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.h"
@@ -55,9 +56,11 @@ long long wait_budget() { return h_wait_budget; }
 // once per device).
 int device_status_ptr(int **out) {
     static int *cache[64] = {};
+    static std::mutex mu;
     int dev = 0;
     SP_CUDA(cudaGetDevice(&dev));
     SP_CHECK(dev >= 0 && dev < 64, SP_ENOTIMPL, "device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
     if (!cache[dev]) {
         void *p = nullptr;
         SP_CUDA(cudaGetSymbolAddress(&p, g_status));
@@ -1076,15 +1079,44 @@ void tc_release(sp_basis *b) {
     b->tc_maps = nullptr;
 }
 
-int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
+using ProjKernel = void (*)(CUtensorMap, ProjParams);
+using ScanKernel = void (*)(CUtensorMap, ScanParams);
+
+// The GEMM1 variant for a basis: A operand in shared memory (2K <= 144) or in tensor memory,
+// exactly 7 microphones (the Table 2 arrays), up to 8, up to 16.
+static ProjKernel proj_kernel_for(const TcLayout &t, int bf, int M) {
+    static const ProjKernel smem_k[6] = {
+        svd_proj_kernel<0, 7, true, 2>, svd_proj_kernel<0, 8, false, 2>, svd_proj_kernel<0, 16, false, 1>,
+        svd_proj_kernel<1, 7, true, 2>, svd_proj_kernel<1, 8, false, 2>, svd_proj_kernel<1, 16, false, 1>};
+    static const ProjKernel tm_k[6] = {
+        svd_proj_tm_kernel<0, 7, true, 2>, svd_proj_tm_kernel<0, 8, false, 2>, svd_proj_tm_kernel<0, 16, false, 1>,
+        svd_proj_tm_kernel<1, 7, true, 2>, svd_proj_tm_kernel<1, 8, false, 2>, svd_proj_tm_kernel<1, 16, false, 1>};
+    const int which = bf * 3 + (M == 7 ? 0 : M <= 8 ? 1 : 2);
+    return t.n1 <= kMaxN1Smem ? smem_k[which] : tm_k[which];
+}
+
+// D tiles in flight of the scan: four, two when the Z tile and four D tiles would not fit (2K > 256)
+static int scan_ring_for(const TcLayout &t) {
+    return 3 * t.k2_atoms * kAtomBytes + 128 * kCap * 4 <= 216 * 1024 ? kRingMax : 2;
+}
+
+static ScanKernel scan_kernel_for(const TcLayout &t, int bf) {
+    static const ScanKernel k[4] = {svd_scan_kernel<0, kRingMax>, svd_scan_kernel<0, 2>, svd_scan_kernel<1, kRingMax>,
+                                    svd_scan_kernel<1, 2>};
+    return k[bf * 2 + (scan_ring_for(t) == kRingMax ? 0 : 1)];
+}
+
+int prepare_tc(const sp_basis *b, int prec) {
+    const TcLayout &t = b->tc;
+    if (t.n1 <= 0 || !b->tc_maps) return SP_OK;
+    const int bf = prec == SP_PREC_BF16 ? 1 : 0;
+    cudaFuncAttributes a;
+    const void *k1 = (const void *)proj_kernel_for(t, bf, b->st->M);
+    const void *k2 = (const void *)scan_kernel_for(t, bf);
+    SP_CUDA(cudaFuncGetAttributes(&a, k1));
+    SP_CUDA(cudaFuncGetAttributes(&a, k2));
+    SP_TRY(ensure_max_smem(k1));
+    return ensure_max_smem(k2);
 }
 
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
@@ -1110,21 +1142,12 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     p.zn2_out = zn2_out;
     p.n_tiles = (int)(((long long)T + 127) / 128);
     const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
-    // variants: exactly 7 microphones (the Table 2 arrays), up to 8, up to 16
-    const int which = bf * 3 + (p.M == 7 ? 0 : p.M <= 8 ? 1 : 2);
+    const ProjKernel kern = proj_kernel_for(t, bf, p.M);
     if (t.n1 <= kMaxN1Smem) {
         // A operand in shared memory: two stages of A (48 KB) and V (3 atoms of n1 rows)
         const int smem = 2 * 3 * kAtomBytes + 2 * 3 * t.n1 * 128 + 128 + 1024;
         SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
-        void (*const kerns[6])(CUtensorMap, ProjParams) = {
-            svd_proj_kernel<0, 7, true, 2>, svd_proj_kernel<0, 8, false, 2>, svd_proj_kernel<0, 16, false, 1>,
-            svd_proj_kernel<1, 7, true, 2>, svd_proj_kernel<1, 8, false, 2>, svd_proj_kernel<1, 16, false, 1>};
-        auto kern = kerns[which];
-        static bool attr[6] = {false, false, false, false, false, false};
-        if (!attr[which]) {
-            SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-            attr[which] = true;
-        }
+        SP_TRY(ensure_max_smem((const void *)kern));
         // at least 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM
         const int smem_launch = std::max(smem, 120 * 1024);
         kern<<<grid, kProjThreads, smem_launch, s>>>(maps->v[bf], p);
@@ -1140,16 +1163,7 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
         SP_CHECK(p.n_aslot >= 2 && p.n_vslot >= 2, SP_ENOTIMPL, "tensor-core plan: too few pipeline stages");
         const int smem = p.n_vslot * b_stage + 256 + 1024;
         SP_CHECK(smem <= 232448, SP_ENOTIMPL, "shared-memory plan exceeds 227 KB");
-        void (*const kerns[6])(CUtensorMap, ProjParams) = {
-            svd_proj_tm_kernel<0, 7, true, 2>, svd_proj_tm_kernel<0, 8, false, 2>,
-            svd_proj_tm_kernel<0, 16, false, 1>, svd_proj_tm_kernel<1, 7, true, 2>,
-            svd_proj_tm_kernel<1, 8, false, 2>, svd_proj_tm_kernel<1, 16, false, 1>};
-        auto kern = kerns[which];
-        static bool attr[6] = {false, false, false, false, false, false};
-        if (!attr[which]) {
-            SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-            attr[which] = true;
-        }
+        SP_TRY(ensure_max_smem((const void *)kern));
         kern<<<grid, kProjThreads, std::max(smem, 120 * 1024), s>>>(maps->v[bf], p);
     }
     SP_CUDA(cudaGetLastError());
@@ -1189,20 +1203,12 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     p.ovf_list = reinterpret_cast<int32_t *>(w + 256);
     p.ovf_keys = reinterpret_cast<unsigned long long *>(w + 256 + ((size_t)T * 4 + 255) / 256 * 256);
     SP_CUDA(cudaMemsetAsync(p.ovf_count, 0, sizeof(int), s));
-    // four D tiles in flight, two when the Z tile and four D tiles would not fit (2K > 256)
-    const int ring = 3 * t.k2_atoms * kAtomBytes + 128 * kCap * 4 <= 216 * 1024 ? kRingMax : 2;
+    const int ring = scan_ring_for(t);
     const int smem = t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 128 * kCap * 4 + 128 * 4 +
                      (4 * ring + 3) * 8 + 1024;
     SP_CHECK(smem <= 232448, SP_ENOTIMPL, "scan: shared-memory plan exceeds 227 KB");
-    const int which = bf * 2 + (ring == kRingMax ? 0 : 1);
-    void (*const kerns[4])(CUtensorMap, ScanParams) = {svd_scan_kernel<0, kRingMax>, svd_scan_kernel<0, 2>,
-                                                       svd_scan_kernel<1, kRingMax>, svd_scan_kernel<1, 2>};
-    auto kern = kerns[which];
-    static bool attr[4] = {false, false, false, false};
-    if (!attr[which]) {
-        SP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-        attr[which] = true;
-    }
+    const ScanKernel kern = scan_kernel_for(t, bf);
+    SP_TRY(ensure_max_smem((const void *)kern));
     const unsigned grid = (unsigned)(((long long)T + 127) / 128);
     kern<<<grid, kScanThreads, smem, s>>>(maps->d[bf], p);
     SP_CUDA(cudaGetLastError());

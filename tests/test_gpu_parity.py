@@ -4,7 +4,8 @@ Tolerances (scores are normalised by L = P(N/2+1), the bound on |Y_q|):
   * TDOA table: bit-exact.  W, PHAT: FP32 rounding (<= 2e-7 absolute, unit-modulus values).
   * argmax indices: identical direction class wherever the oracle's top-2 margin exceeds
     1e-4 (relative), and >= 99.5 % class agreement over all frames.
-  * FP32 scores: |dY| <= 1e-5 L.  FP16 / BF16 after FP32 rescoring: 2e-3 L / 1e-2 L.
+  * FP32 scores (SRP, FP32 SVD-PHAT, online step 4): |dY| <= 1e-5 L.  FP16 / BF16 search
+    scores after FP32 rescoring: 2e-3 L / 1e-2 L.
 """
 import numpy as np
 import pytest
@@ -179,11 +180,10 @@ def test_localize_srp(name, T):
     idx = idx.cpu().numpy()
     _agree(d, idx, d["Ysrp"])
     ref = d["Ysrp"][np.arange(T), idx]
-    # 2L sequential FP32 fused multiply-adds with partial sums up to L: independent roundings
-    # give a standard deviation of about u L sqrt(2L) / 3 (u = 2^-24); 2 u L sqrt(2L) is six of
-    # them, and 1e-5 L covers the FP32 steering matrix
+    # FP32 scores within 1e-5 L of FP64 (the kernel sums blocks of 256 complex terms and then
+    # the block sums, so its rounding error is about u L sqrt(L / 256), u = 2^-24)
     L = d["L"]
-    assert np.max(np.abs(best.cpu().numpy() - ref)) <= 1e-5 * L + 2 * 2.0**-24 * L * np.sqrt(2 * L)
+    assert np.max(np.abs(best.cpu().numpy() - ref)) <= 1e-5 * L
 
 
 @pytest.mark.parametrize("name,T", CONFIGS)
@@ -198,7 +198,7 @@ def test_localize_svd_exhaustive(name, T, prec, tol):
     assert np.all(d["cls"][idx] == idx)           # the lowest index of the winning class
     assert np.max(np.abs(proj.cpu().numpy() - d["Ysvd"][np.arange(T), idx])) <= tol * d["L"]
     sref = O.score_row(d["tau"], idx, d["X"], d["wl"]["N"])       # Algorithm 1 online step 4
-    assert np.max(np.abs(score.cpu().numpy() - sref)) <= 2e-5 * d["L"]
+    assert np.max(np.abs(score.cpu().numpy() - sref)) <= 1e-5 * d["L"]
 
 
 @pytest.mark.parametrize("name,T", CONFIGS)
@@ -315,7 +315,8 @@ def test_bounded_wait_reports_timeout():
 
 def test_bench_workload_full_size_sampled():
     """The measured workload at full size (65,536 frames, planar array, Q = 2562) in the launch
-    configuration the benchmark times; 384 sampled frames are checked against the oracle."""
+    configuration the benchmark times; 2,048 sampled frames are checked against the oracle
+    (enough for the >= 99.5 % agreement rule to apply)."""
     import __graft_entry__
     __graft_entry__.build()
     wl = I.workload("planar_q2562")
@@ -323,7 +324,7 @@ def test_bench_workload_full_size_sampled():
     b = sp.svd_reduce(st, wl["delta"])
     frames = torch.from_numpy(wl["frames"]).cuda()
     rng = np.random.default_rng(14)
-    sel = np.sort(rng.choice(frames.shape[0], 384, replace=False))
+    sel = np.sort(rng.choice(frames.shape[0], 2048, replace=False))
     tau = O.tdoa_farfield(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"])
     W = O.steering(tau, wl["N"])
     ob = O.svd_basis(W, wl["delta"])
@@ -337,7 +338,7 @@ def test_bench_workload_full_size_sampled():
         idx = idx.cpu().numpy()[sel]
         _agree(d, idx, Y)
         sref = O.score_row(tau, idx, X, wl["N"])
-        assert np.max(np.abs(score.cpu().numpy()[sel] - sref)) <= 2e-5 * W.shape[1]
+        assert np.max(np.abs(score.cpu().numpy()[sel] - sref)) <= 1e-5 * W.shape[1]
 
 
 def test_save_load_basis_roundtrip(tmp_path):

@@ -247,6 +247,23 @@ def test_jacobi_matches_lapack_and_reconstructs():
     assert np.max(np.abs((U * lam) @ U.conj().T - G)) < 1e-11 * np.abs(G).max()
 
 
+@pytest.mark.slow
+def test_jacobi_matches_lapack_on_the_q642_line_array_gram():
+    """The 1-D 7-mic line array on the level-3 grid (Q = 642, N = 512, L = 5397): the basis the
+    GPU parity tests take from the oracle's own Jacobi iteration (n = Q = 642) has LAPACK's
+    singular values, rank (Eq. 11) and subspace."""
+    tau = O.tdoa_farfield(I.array_linear_1d(), I.icosphere(3), 16000.0, 343.0)
+    W = O.steering(tau, 512)
+    bj = O.svd_basis(W, 1e-5)
+    assert bj["eig"] == "jacobi"
+    bl = O.svd_basis(W, 1e-5, eig="lapack")
+    assert bj["K"] == bl["K"]
+    assert np.max(np.abs(bj["sigma2"] - bl["sigma2"])) < 1e-11 * bl["sigma2"][0]
+    assert np.sum(bj["sigma2"]) == pytest.approx(W.shape[0] * W.shape[1], rel=1e-12)   # Tr = Q L
+    G = bj["V"].conj().T @ bl["V"]                                                   # same subspace
+    assert np.max(np.abs(G.conj().T @ G - np.eye(bj["K"]))) < 1e-10
+
+
 def _small_W(arr="3d", lvl=2, N=32):
     mic = {"linear": I.array_linear_1d(), "planar": I.array_planar_2d_table(), "3d": I.array_3d()}[arr]
     tau = O.tdoa_farfield(mic, I.icosphere(lvl), 16000.0, 343.0)
