@@ -62,7 +62,10 @@ int ensure_max_smem(const void *kernel) {
     SP_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(g_dev_mu);
     if (done.count({dev, kernel})) return SP_OK;
-    SP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+    cudaFuncAttributes a;   // the 227 KB per block include the kernel's static shared memory
+    SP_CUDA(cudaFuncGetAttributes(&a, kernel));
+    SP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 232448 - (int)a.sharedSizeBytes));
     done.insert({dev, kernel});
     return SP_OK;
 }

@@ -198,7 +198,7 @@ int encode_tmap_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint6
                    uint32_t box_rows);
 // Multiprocessor count of the current device (looked up once per device).
 int num_sms();
-// Raise a kernel's dynamic shared-memory limit to 227 KB on the current device.  The
+// Raise a kernel's shared-memory limit (static + dynamic) to 227 KB on the current device.  The
 // attribute belongs to the device, so it is set once per (device, kernel) pair; a process
 // that drives several GPUs sets it on each.  Thread-safe.
 int ensure_max_smem(const void *kernel);
