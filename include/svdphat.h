@@ -223,6 +223,12 @@ int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
  * proj_score_dev: device float [T] or NULL: the search's own score, Re{D_idx Z} for the
  *                 SVD modes (Re{D^_idx Z^} for the k-d tree), Re{W_idx X} for SRP.
  * Asynchronous on stream; the basis workspace is reused by the next call.
+ *
+ * Frame alignment: frames must be 8-byte aligned.  For 7-microphone arrays the FP16/BF16
+ * path reads 16-byte-aligned frame buffers with TMA (the fast GEMM1 kernel); a buffer 8 bytes
+ * off a 16-byte boundary runs a register-fed GEMM1 whose FP32 summation order differs, so
+ * scores can differ in the last bits (and an index only where two scores tie that closely).
+ * Results are bit-identical between calls on buffers of the same alignment.
  * --------------------------------------------------------------------------------- */
 int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec,
                 int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream);

@@ -131,6 +131,8 @@ struct sp_basis {
     sp::DevBuf Dc32r;                   // D rows of the class representatives [n_classes][K]
     sp::TcLayout tc;
     sp::DevBuf Vtc[2];                  // GEMM1 B operand, fp16 [0] / bf16 [1]: [n1][row_elems]
+    sp::DevBuf Vbm[2];                  // the same with bin-major chunks (pair p, bin b of a chunk at
+                                        // element 48 b + 2 p) for the TMA-fed GEMM1 (M = 7); else empty
     sp::DevBuf Dtc[2];                  // GEMM2 B operand, fp16 / bf16: [Q][k2_atoms*64]
     float v_scale = 1.f;                // Vtc holds V * v_scale
     void *tc_maps = nullptr;            // TMA descriptors of Vtc / Dtc (owned)
@@ -187,6 +189,13 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
 int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
                   cudaStream_t s);
 int tc_prepare(sp_basis *b);
+// TMA descriptor of the bin-major GEMM1 B operand (Vbm) of a basis, fp16 (bf16 = 0) or bf16;
+// null where the basis has none
+const CUtensorMap *tc_vmap_binmajor(const sp_basis *b, int bf16);
+// GEMM1 with the STFT fed by TMA (7 microphones, odd B, 16-byte-aligned frames); SP_ENOTIMPL
+// where its plan does not apply, and the caller then runs svd_proj_kernel / svd_proj_tm_kernel
+int launch_svd_proj_tma(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
+                        cudaStream_t s, int max_ctas);
 // Load the kernels a localisation of this basis / array would launch on the current device
 // and set their shared-memory limits (what their first launches would otherwise do).
 int prepare_tc(const sp_basis *b, int prec);
@@ -197,6 +206,10 @@ int prepare_step4(const sp_steering *st);
 int encode_tmap_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint64_t rows, uint32_t box_inner,
                    uint32_t box_rows);
 // Multiprocessor count of the current device (looked up once per device).
+// 2-D tensor map of a float32 array with rows row_stride_bytes apart (a multiple of 16),
+// no swizzle, zero fill outside [inner] x [rows], box {box_inner, box_rows}
+int encode_tmap_f32_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t row_stride_bytes,
+                       uint32_t box_inner, uint32_t box_rows);
 int num_sms();
 // Raise a kernel's shared-memory limit (static + dynamic) to 227 KB on the current device.  The
 // attribute belongs to the device, so it is set once per (device, kernel) pair; a process

@@ -1000,8 +1000,24 @@ int encode_tmap_2d(CUtensorMap *map, void *base, int bf16, uint64_t inner, uint6
     return SP_OK;
 }
 
+int encode_tmap_f32_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t row_stride_bytes,
+                       uint32_t box_inner, uint32_t box_rows) {
+    EncodeTiledFn enc = get_encode();
+    SP_CHECK(enc != nullptr, SP_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {row_stride_bytes};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    SP_CHECK(r == CUDA_SUCCESS, SP_ECUDA, "cuTensorMapEncodeTiled (f32) failed (" + std::to_string((int)r) + ")");
+    return SP_OK;
+}
+
 struct TcMaps {
-    CUtensorMap v[2], d[2];
+    CUtensorMap v[2], d[2], vbm[2];
+    bool has_vbm = false;
 };
 
 int tc_prepare(sp_basis *b) {
@@ -1038,6 +1054,29 @@ int tc_prepare(sp_basis *b) {
                     }
                 }
             }
+    // bin-major copy for the TMA-fed GEMM1 of 7-microphone arrays (P = 21 <= 24: one stage per
+    // chunk; pair p, bin bb of chunk c at element c * 192 + 48 bb + 2 p)
+    const bool bm = st->M == 7 && (B & 1) && t.n1 <= 224;
+    std::vector<float> vbm;
+    if (bm) {
+        vbm.assign(nv, 0.f);
+        for (int c = 0; c < t.n_chunks; ++c)
+            for (int p = 0; p < P; ++p)
+                for (int bb = 0; bb < kChunkBins; ++bb) {
+                    const int k = c * kChunkBins + bb;
+                    if (k >= B) break;
+                    const size_t l = (size_t)p * B + k;
+                    const size_t e = (size_t)c * kGroupElems + 48 * bb + 2 * p;
+                    for (int kk = 0; kk < K; ++kk) {
+                        const double vr = b->V[(l * K + kk) * 2] * b->v_scale;
+                        const double vi = b->V[(l * K + kk) * 2 + 1] * b->v_scale;
+                        vbm[(size_t)(2 * kk) * t.row_elems + e] = (float)vr;
+                        vbm[(size_t)(2 * kk) * t.row_elems + e + 1] = (float)vi;
+                        vbm[(size_t)(2 * kk + 1) * t.row_elems + e] = (float)-vi;
+                        vbm[(size_t)(2 * kk + 1) * t.row_elems + e + 1] = (float)vr;
+                    }
+                }
+    }
     const int dcols = t.k2_atoms * kAtomElems;
     const int Qr = (int)st->reps.size();
     std::vector<float> df((size_t)Qr * dcols, 0.f);
@@ -1065,6 +1104,18 @@ int tc_prepare(sp_basis *b) {
         SP_CUDA(cudaMemcpy(b->Dtc[prec].p, hd.data(), hd.size() * 2, cudaMemcpyHostToDevice));
         int rc = encode_tmap_2d(&maps->v[prec], b->Vtc[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.v_box);
         if (rc == SP_OK) rc = encode_tmap_2d(&maps->d[prec], b->Dtc[prec].p, prec, dcols, Qr, kAtomElems, kN2);
+        if (rc == SP_OK && bm) {
+            for (size_t i = 0; i < nv; ++i) {
+                if (prec == 0) { __half h = __float2half_rn(vbm[i]); hv[i] = *reinterpret_cast<uint16_t *>(&h); }
+                else { __nv_bfloat16 h = __float2bfloat16_rn(vbm[i]); hv[i] = *reinterpret_cast<uint16_t *>(&h); }
+            }
+            rc = b->Vbm[prec].reserve(nv * 2);
+            if (rc == SP_OK && cudaMemcpy(b->Vbm[prec].p, hv.data(), nv * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = fail(SP_ECUDA, "tc_prepare: copy of the bin-major V");
+            if (rc == SP_OK)
+                rc = encode_tmap_2d(&maps->vbm[prec], b->Vbm[prec].p, prec, t.row_elems, t.n1, kAtomElems, t.v_box);
+            maps->has_vbm = rc == SP_OK;
+        }
         if (rc != SP_OK) {
             delete maps;
             return rc;
@@ -1072,6 +1123,11 @@ int tc_prepare(sp_basis *b) {
     }
     b->tc_maps = maps;
     return SP_OK;
+}
+
+const CUtensorMap *tc_vmap_binmajor(const sp_basis *b, int bf16) {
+    const TcMaps *m = reinterpret_cast<const TcMaps *>(b->tc_maps);
+    return m && m->has_vbm ? &m->vbm[bf16 ? 1 : 0] : nullptr;
 }
 
 void tc_release(sp_basis *b) {
@@ -1142,6 +1198,10 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     p.zn2_out = zn2_out;
     p.n_tiles = (int)(((long long)T + 127) / 128);
     const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
+    {   // the TMA-fed kernel for 7-microphone arrays where its plan applies
+        const int rc = launch_svd_proj_tma(b, frames, T, prec, z_out, zn2_out, s, max_ctas);
+        if (rc != SP_ENOTIMPL) return rc;
+    }
     const ProjKernel kern = proj_kernel_for(t, bf, p.M);
     if (t.n1 <= kMaxN1Smem) {
         // A operand in shared memory: two stages of A (48 KB) and V (3 atoms of n1 rows)

@@ -173,6 +173,32 @@ def test_project(name, T, prec, tol):
     assert np.max(np.abs(Zg - d["Z"])) <= bound
 
 
+@pytest.mark.parametrize("name,T", [("linear_q642", 100), ("planar_q2562", 777), ("array3d_q10242", 256)])
+@pytest.mark.parametrize("prec,tol", [("fp16", 1e-4), ("bf16", 1e-3)])
+def test_project_tma_fed_and_register_fed_kernels(name, T, prec, tol):
+    """The 7-microphone arrays run GEMM1 with the STFT fed by TMA when the frames are 16-byte
+    aligned, and with per-thread loads otherwise (a buffer 8 bytes off): both give the oracle's
+    Z (Eq. 12) within the tensor-core bound, and the two paths agree with each other."""
+    d = _setup(name, T)
+    b = oracle_basis_in_library(d)
+    fr = d["frames"]
+    buf = torch.empty(fr.numel() + 1, dtype=torch.complex64, device=fr.device)
+    shifted = buf[1:].view(fr.shape)              # 8 bytes past a 256-byte boundary
+    shifted.copy_(fr)
+    assert fr.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    Za = sp.project(b, fr, prec).cpu().numpy()
+    Zb = sp.project(b, shifted, prec).cpu().numpy()
+    L = d["L"]
+    bound = tol * np.sqrt(L) + (2 * L / 16) * 2.0**-23 * np.sqrt(L)
+    assert np.max(np.abs(Za - d["Z"])) <= bound
+    assert np.max(np.abs(Zb - d["Z"])) <= bound
+    assert np.max(np.abs(Za - Zb)) <= 2 * bound
+    # odd frame counts leave the last row of microphone pairs half outside the buffer
+    for t in (1, 3, 129):
+        Zt = sp.project(b, fr[:t].contiguous(), prec).cpu().numpy()
+        assert np.max(np.abs(Zt - Za[:t])) <= 2 * bound
+
+
 @pytest.mark.parametrize("name,T", CONFIGS)
 def test_localize_srp(name, T):
     d = _setup(name, T)
@@ -243,12 +269,20 @@ def test_tree_shape():
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
 def test_ragged_batches_are_consistent(prec):
+    """Sub-batches in 16-byte-aligned buffers (copies) give bit-identical results; views that
+    start 8 bytes off a 16-byte boundary run the register-fed GEMM1 (another FP32 summation
+    order) and agree within the FP32 bound."""
     d = _setup("planar_q2562", 777)
     full, _, pfull = sp.localize(d["b"], d["frames"], "svd_exhaustive", prec, score=False)
     for lo, hi in [(0, 1), (5, 132), (128, 256), (700, 777), (3, 3)]:
-        idx, _, pj = sp.localize(d["b"], d["frames"][lo:hi].contiguous(), "svd_exhaustive", prec, score=False)
+        idx, _, pj = sp.localize(d["b"], d["frames"][lo:hi].clone(), "svd_exhaustive", prec, score=False)
         assert torch.equal(idx, full[lo:hi])
         assert torch.equal(pj, pfull[lo:hi])
+        view = d["frames"][lo:hi]                  # no copy: 8 bytes off for odd lo
+        iv, _, pv = sp.localize(d["b"], view, "svd_exhaustive", prec, score=False)
+        if hi > lo:
+            assert np.max(np.abs(pv.cpu().numpy() - pj.cpu().numpy())) <= 1e-5 * d["L"]
+            assert np.mean((iv == idx).cpu().numpy()) >= 0.99
 
 
 def test_zero_and_nan_frames():
