@@ -15,14 +15,21 @@
 // row when 7T is odd) reads as zero, and a zero spectrum entry is a zero cross spectrum
 // (Eq. 3 with the |X|^2 < 1e-30 rule), so the producers need no bounds logic.
 //
-// Producers.  Eight warps in two groups; group g takes the chunks g, g + 2, ... of the
+// Producers.  Twelve warps in three groups; group g takes the chunks g, g + 3, ... of the
 // CTA's sequence and owns A stage g in tensor memory (96 columns: pair p, bin b of the chunk
 // at column 24 b + p, (Re, Im) packed as two 16-bit values; V is stored in the same
 // bin-major order, pairs 21-23 of a bin zero).  A thread is one frame (its TMEM lane): it
 // copies its 7 x 4 raw values out of the raw slot (releasing the slot at once), then per bin
 // normalises the 7 values, forms the 21 pairs and writes the bin's 24 columns with three
-// 8-column tcgen05.st.  One warp streams V atoms by TMA, one streams raw slots, one issues the MMAs
-// (A from tensor memory, B = V from shared memory, 12 K16 steps per chunk), four drain Z.
+// 8-column tcgen05.st.  The group that produced a tile's last chunk then drains that tile's
+// Z from tensor memory to global memory.  One warp streams raw slots by TMA, one V atoms, one
+// issues the MMAs (A from tensor memory, B = V from shared memory, 12 K16 steps per chunk).
+// Fifteen warps leave every thread 128 registers (a scheduler holds at most four warps).
+// V arrives in three stages where shared memory allows (two for wide bases): every SM reads the
+// same 2.4 MB of V in the same chunk order, and its L2 latency, not the STFT's, is the one the
+// third stage hides (measured 336 -> 313 us per 65,536 frames).  What bounds the kernel then
+// is the TMA path for the STFT slices: rows of 32-80 bytes, about 3.5-4.2 TB/s even when the
+// slices are resident in L2.
 //
 // Every mbarrier wait is bounded; a wait that gives up records an error in the status word
 // and the CTA drains its in-flight TMA loads and MMAs before it frees tensor memory.
@@ -42,9 +49,9 @@ namespace {
 constexpr int kM = 7;                    // microphones
 constexpr int kP = 21;                   // pairs
 constexpr int kSteps = 12;               // K16 MMA steps per chunk (4 bins x 24 pair slots)
-constexpr int kGroups = 2;               // producer groups = A stages in tensor memory
+constexpr int kGroups = 3;               // producer groups = A stages in tensor memory
 constexpr int kAStageCols = 96;          // TMEM columns per A stage
-constexpr int kEpiWarp0 = 8, kVWarp = 12, kRawWarp = 13, kMmaWarp = 14;
+constexpr int kRawWarp = 12, kVWarp = 13, kMmaWarp = 14;
 constexpr int kThreads = 15 * 32;
 constexpr int kTileRows = 64 * kM;       // 448 rows of two microphone rows per 128 frames
 constexpr int kBoxRows = kTileRows / 2;  // 224 (a box spans at most 256 rows)
@@ -53,13 +60,11 @@ constexpr long long kDrainBudget = 4000000000LL;
 
 struct Params {
     int T, B, n_chunks, n1, K, n_tiles;
-    int cpr;            // chunks per raw slot (1 or 2)
-    int n_raw;          // raw slots
-    int n_raw_loads;    // raw slot loads per tile = ceil(n_chunks / cpr)
+    int n_raw_loads;    // raw slot loads per tile = ceil(n_chunks / CPR)
     int n_zbuf;         // Z accumulators in tensor memory (1 or 2)
     int z_cols;         // TMEM column offset of the second Z accumulator
     int a_col0;         // first A stage column
-    int e0_bytes;       // bytes of the e = 0 region of a raw slot (448 rows x 32 cpr)
+    int e0_bytes;       // bytes of the e = 0 region of a raw slot (448 rows x 32 CPR)
     int slot_bytes;     // bytes of a raw slot
     int v_stage_bytes;  // bytes of a V stage (3 atoms x n1 rows x 128)
     float inv_vscale;
@@ -96,39 +101,41 @@ constexpr Pairs7 make_pairs7() {
     return t;
 }
 
-// 15 warps x 128 registers fit the 64K registers of an SM (a producer holds its 7 x 4 raw
-// values, 56 registers, while it forms the pairs bin by bin)
-template <int BF16>
+// CPR chunks per raw slot, NRAW raw slots, NV V stages (3 V stages and 3 raw slots of one chunk
+// where shared memory allows, else 2 V stages)
+template <int BF16, int CPR, int NRAW, int NV>
 __global__ void __maxnreg__(128)
     svd_proj_tma_kernel(const __grid_constant__ CUtensorMap tmap_v, const __grid_constant__ CUtensorMap tmap_e0,
                         const __grid_constant__ CUtensorMap tmap_e1, const Params prm) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n1 = prm.n1, cpr = prm.cpr, n_raw = prm.n_raw;
-    uint8_t *vbuf = smem;                                   // 2 V stages
-    uint8_t *rawbuf = smem + 2 * prm.v_stage_bytes;         // n_raw raw slots
-    uint64_t *bars = reinterpret_cast<uint64_t *>(rawbuf + n_raw * prm.slot_bytes);
+    const int n1 = prm.n1;
+    uint8_t *vbuf = smem;                                   // NV V stages
+    uint8_t *rawbuf = smem + NV * prm.v_stage_bytes;        // NRAW raw slots
+    uint64_t *bars = reinterpret_cast<uint64_t *>(rawbuf + NRAW * prm.slot_bytes);
     uint64_t *full_raw = bars, *empty_raw = bars + 4;       // up to 4 raw slots
-    uint64_t *full_a = bars + 8, *empty_a = bars + 8 + kGroups;
-    uint64_t *full_v = bars + 14, *empty_v = bars + 16;
-    uint64_t *zfull = bars + 18, *zempty = bars + 20, *drain = bars + 22;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 23);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 24);
+    uint64_t *full_a = bars + 8, *empty_a = bars + 11;      // 3 A stages
+    uint64_t *full_v = bars + 14, *empty_v = bars + 17;
+    uint64_t *zfull = bars + 20, *zempty = bars + 22, *drain = bars + 24;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 25);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 26);
     const long long budget = prm.budget;
 
     if (tid == 0) {
-        for (int i = 0; i < n_raw; ++i) {
+        for (int i = 0; i < NRAW; ++i) {
             ptx::mbar_init(&full_raw[i], 1);
-            ptx::mbar_init(&empty_raw[i], 4 * cpr);
+            ptx::mbar_init(&empty_raw[i], 4 * CPR);
         }
         for (int i = 0; i < kGroups; ++i) {
             ptx::mbar_init(&full_a[i], 4);
             ptx::mbar_init(&empty_a[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NV; ++i) {
             ptx::mbar_init(&full_v[i], 1);
             ptx::mbar_init(&empty_v[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&zfull[i], 1);
             ptx::mbar_init(&zempty[i], 128);
         }
@@ -151,33 +158,37 @@ __global__ void __maxnreg__(128)
     const uint32_t tmem = *tmem_slot;
     const int n_chunks = prm.n_chunks;
     const int my_tiles = prm.n_tiles > (int)blockIdx.x ? (prm.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int n_stages = my_tiles * n_chunks;   // < 2^31: at most 2^21 tiles of 128 frames per launch
     auto give_up = [&]() {
         *abort_flag = 1;
         atomicOr(prm.status, 1);
     };
 
-    if (warp < kEpiWarp0) {
+    if (warp < kRawWarp) {
         // -------- producers: group g, TMEM lane quarter q4, frame row f
         constexpr Pairs7 tab = make_pairs7();   // compile-time register indices below
         const int q4 = warp & 3, grp = warp >> 2;
         const int f = q4 * 32 + lane;
-        const int pitch0 = 32 * cpr, pitch1 = 32 * cpr + 16;
+        constexpr int pitch0 = 32 * CPR, pitch1 = 32 * CPR + 16;
         const uint32_t raw_base = ptx::smem_u32(rawbuf);
-        const uint32_t a_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(prm.a_col0 + grp * kAStageCols);
-        int use = 0;   // uses of this group's A stage
-        for (int j = grp; j < n_stages; j += kGroups, ++use) {
-            const int li = j / n_chunks, c = j - li * n_chunks;
-            const int h = li * prm.n_raw_loads + c / cpr;
-            const int slot = h % n_raw;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q4 * 32) << 16);
+        const uint32_t a_base = lane_addr + (uint32_t)(prm.a_col0 + grp * kAStageCols);
+        // this group's chunks j = grp, grp + 3, ... of the CTA's sequence as (tile li, chunk c)
+        int li = 0, c = grp;
+        while (c >= n_chunks) {
+            c -= n_chunks;
+            ++li;
+        }
+        for (int use = 0; li < my_tiles; ++use) {
+            const int h = li * prm.n_raw_loads + c / CPR;   // raw slot load of this chunk
+            const int slot = h % NRAW;
             if (ptx::warp_flag(abort_flag)) break;
-            if (!ptx::mbar_wait_warp(&full_raw[slot], (uint32_t)((h / n_raw) & 1), budget)) {
+            if (!ptx::mbar_wait_warp(&full_raw[slot], (uint32_t)((h / NRAW) & 1), budget)) {
                 if (lane == 0) give_up();
                 break;
             }
             // raw values of this frame's 4 bins for every microphone, then release the slot
             float2 x[kM][4];
-            const uint32_t sb = raw_base + (uint32_t)(slot * prm.slot_bytes + (c % cpr) * 32);
+            const uint32_t sb = raw_base + (uint32_t)(slot * prm.slot_bytes + (c % CPR) * 32);
 #pragma unroll
             for (int m = 0; m < kM; ++m) {
                 // microphone row u = 7 f + m is half u & 1 of raw row u >> 1 (bin 0 of the slot's
@@ -193,7 +204,7 @@ __global__ void __maxnreg__(128)
             __syncwarp();
             if (lane == 0) {
                 // the last chunk of a tile may be alone in its slot: it arrives for both
-                const bool alone = cpr == 2 && c == n_chunks - 1 && (n_chunks & 1);
+                const bool alone = CPR == 2 && c == n_chunks - 1 && (n_chunks & 1);
                 ptx::mbar_arrive_cnt(&empty_raw[slot], alone ? 2u : 1u);
             }
             if (!ptx::mbar_wait_warp(&empty_a[grp], (uint32_t)((use & 1) ^ 1), budget)) {
@@ -232,79 +243,58 @@ __global__ void __maxnreg__(128)
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&full_a[grp]);
-        }
-    } else if (warp < kVWarp) {
-        // -------- epilogue: Z of each finished tile, TMEM -> FP32 global
-        const int q4 = warp & 3;
-        const int r = q4 * 32 + lane;
-        for (int li = 0; li < my_tiles; ++li) {
-            const int zb = prm.n_zbuf == 2 ? (li & 1) : 0;
-            const uint32_t zpar = prm.n_zbuf == 2 ? ((li >> 1) & 1) : (li & 1);
-            if (ptx::warp_flag(abort_flag)) break;
-            if (!ptx::mbar_wait_warp(&zfull[zb], zpar, budget)) {
-                if (lane == 0) give_up();
-                break;
-            }
-            ptx::tc_fence_after();
-            const long long frame = (long long)((int)blockIdx.x + li * (int)gridDim.x) * 128 + r;
-            const bool live = frame < prm.T;
-            float2 *zo = prm.z_out + (size_t)(live ? frame : 0) * prm.K;
-            float zn2 = 0.f;
-            for (int c0 = 0; c0 < n1; c0 += 32) {
-                float v[32];
-                ptx::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(zb * prm.z_cols + c0), v);
-                if (live) {
+            if (c == n_chunks - 1) {
+                // this group produced the tile's last chunk: drain the tile's Z (TMEM -> FP32 global)
+                const int zb = prm.n_zbuf == 2 ? (li & 1) : 0;
+                const uint32_t zpar = prm.n_zbuf == 2 ? ((li >> 1) & 1) : (li & 1);
+                if (!ptx::mbar_wait_warp(&zfull[zb], zpar, budget)) {
+                    if (lane == 0) give_up();
+                    break;
+                }
+                ptx::tc_fence_after();
+                const long long frame = (long long)((int)blockIdx.x + li * (int)gridDim.x) * 128 + f;
+                const bool live = frame < prm.T;
+                float2 *zo = prm.z_out + (size_t)(live ? frame : 0) * prm.K;
+                float zn2 = 0.f;
+                for (int c0 = 0; c0 < n1; c0 += 32) {
+                    float v[32];
+                    ptx::tmem_ld32(lane_addr + (uint32_t)(zb * prm.z_cols + c0), v);
+                    if (live) {
 #pragma unroll
-                    for (int i = 0; i < 32; i += 2) {
-                        const int kk = (c0 + i) >> 1;
-                        if (kk < prm.K) {
-                            const float2 z = make_float2(v[i] * prm.inv_vscale, v[i + 1] * prm.inv_vscale);
-                            zo[kk] = z;
-                            zn2 = fmaf(z.x, z.x, fmaf(z.y, z.y, zn2));
+                        for (int i = 0; i < 32; i += 2) {
+                            const int kk = (c0 + i) >> 1;
+                            if (kk < prm.K) {
+                                const float2 z = make_float2(v[i] * prm.inv_vscale, v[i + 1] * prm.inv_vscale);
+                                zo[kk] = z;
+                                zn2 = fmaf(z.x, z.x, fmaf(z.y, z.y, zn2));
+                            }
                         }
                     }
                 }
+                if (prm.zn2_out && live) prm.zn2_out[frame] = zn2;
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&zempty[zb]);
             }
-            if (prm.zn2_out && live) prm.zn2_out[frame] = zn2;
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&zempty[zb]);
-        }
-    } else if (warp == kVWarp) {
-        // -------- V atoms of each chunk (3 atoms of n1 rows), two stages
-        if (lane == 0) {
-            long long issued = -1;
-            for (long long j = 0; j < n_stages; ++j) {
-                const int s = (int)(j & 1);
-                if (*abort_flag) break;
-                if (!ptx::mbar_wait(&empty_v[s], (uint32_t)(((j >> 1) & 1) ^ 1), budget)) {
-                    give_up();
-                    break;
-                }
-                const int c = (int)(j % n_chunks);
-                ptx::mbar_arrive_expect_tx(&full_v[s], (uint32_t)prm.v_stage_bytes);
-                uint8_t *Vs = vbuf + s * prm.v_stage_bytes;
-                for (int a = 0; a < 3; ++a)
-                    ptx::tma_load_2d(Vs + a * n1 * 128, &tmap_v, &full_v[s], c * kChunkElems + a * 64, 0);
-                issued = j;
+            c += kGroups;
+            while (c >= n_chunks) {
+                c -= n_chunks;
+                ++li;
             }
-            for (long long j = std::max(0LL, issued - 1); j <= issued; ++j)
-                ptx::mbar_wait(&full_v[j & 1], (uint32_t)((j >> 1) & 1), kDrainBudget);
         }
-        __syncwarp();
     } else if (warp == kRawWarp) {
-        // -------- raw STFT slots: cpr chunks of one tile, both halves of its 448 rows
+        // -------- raw STFT slots: CPR chunks of one tile, both halves of its 448 rows
         if (lane == 0) {
             long long issued = -1;
             const long long n_loads = (long long)my_tiles * prm.n_raw_loads;
-            const int e0_box = kBoxRows * 32 * cpr, e1_box = kBoxRows * (32 * cpr + 16);
+            const int e0_box = kBoxRows * 32 * CPR, e1_box = kBoxRows * (32 * CPR + 16);
             for (long long h = 0; h < n_loads; ++h) {
-                const int slot = (int)(h % n_raw);
+                const int slot = (int)(h % NRAW);
                 if (*abort_flag) break;
-                if (!ptx::mbar_wait(&empty_raw[slot], (uint32_t)(((h / n_raw) & 1) ^ 1), budget)) {
+                if (!ptx::mbar_wait(&empty_raw[slot], (uint32_t)(((h / NRAW) & 1) ^ 1), budget)) {
                     give_up();
                     break;
                 }
-                const int li = (int)(h / prm.n_raw_loads), c0 = (int)(h % prm.n_raw_loads) * cpr;
+                const int li = (int)(h / prm.n_raw_loads), c0 = (int)(h % prm.n_raw_loads) * CPR;
                 const int row0 = ((int)blockIdx.x + li * (int)gridDim.x) * kTileRows;
                 uint8_t *S = rawbuf + slot * prm.slot_bytes;
                 ptx::mbar_arrive_expect_tx(&full_raw[slot], (uint32_t)prm.slot_bytes);
@@ -315,12 +305,35 @@ __global__ void __maxnreg__(128)
                 }
                 issued = h;
             }
-            for (long long h = std::max(0LL, issued - n_raw + 1); h <= issued; ++h)
-                ptx::mbar_wait(&full_raw[h % n_raw], (uint32_t)((h / n_raw) & 1), kDrainBudget);
+            for (long long h = std::max(0LL, issued - NRAW + 1); h <= issued; ++h)
+                ptx::mbar_wait(&full_raw[h % NRAW], (uint32_t)((h / NRAW) & 1), kDrainBudget);
+        }
+        __syncwarp();
+    } else if (warp == kVWarp) {
+        // -------- V atoms of each chunk (3 atoms of n1 rows), NV stages
+        if (lane == 0) {
+            long long issued = -1;
+            const long long n_stages = (long long)my_tiles * n_chunks;
+            for (long long j = 0; j < n_stages; ++j) {
+                const int s = (int)(j % NV);
+                if (*abort_flag) break;
+                if (!ptx::mbar_wait(&empty_v[s], (uint32_t)(((j / NV) & 1) ^ 1), budget)) {
+                    give_up();
+                    break;
+                }
+                const int c = (int)(j % n_chunks);
+                ptx::mbar_arrive_expect_tx(&full_v[s], (uint32_t)prm.v_stage_bytes);
+                uint8_t *Vs = vbuf + s * prm.v_stage_bytes;
+                for (int a = 0; a < 3; ++a)
+                    ptx::tma_load_2d(Vs + a * n1 * 128, &tmap_v, &full_v[s], c * kChunkElems + a * 64, 0);
+                issued = j;
+            }
+            for (long long j = std::max(0LL, issued - NV + 1); j <= issued; ++j)
+                ptx::mbar_wait(&full_v[j % NV], (uint32_t)((j / NV) & 1), kDrainBudget);
         }
         __syncwarp();
     } else {
-        // -------- MMA issue: Z (+)= A[tmem] V[smem], 11 K16 steps per chunk
+        // -------- MMA issue: Z (+)= A[tmem] V[smem], 12 K16 steps per chunk
         if (lane == 0) {
             const uint32_t idesc = ptx::idesc_f16(128, n1, BF16);
             long long j = 0;
@@ -336,9 +349,9 @@ __global__ void __maxnreg__(128)
                 const uint32_t d_tmem = tmem + (uint32_t)(zb * prm.z_cols);
                 bool ok = true;
                 for (int c = 0; c < n_chunks; ++c, ++j) {
-                    const int s = (int)(j % kGroups), v = (int)(j & 1);
+                    const int s = (int)(j % kGroups), v = (int)(j % NV);
                     if (*abort_flag || !ptx::mbar_wait(&full_a[s], (uint32_t)((j / kGroups) & 1), budget) ||
-                        !ptx::mbar_wait(&full_v[v], (uint32_t)((j >> 1) & 1), budget)) {
+                        !ptx::mbar_wait(&full_v[v], (uint32_t)((j / NV) & 1), budget)) {
                         if (!*abort_flag) give_up();
                         ok = false;
                         break;
@@ -380,7 +393,7 @@ int launch_svd_proj_tma(const sp_basis *b, const void *frames, int T, int prec, 
     const TcLayout &t = b->tc;
     const int B = st->B;
     // the plan: exactly 7 microphones, odd B (the 16-byte boundary falls one complex before
-    // the second half of a row), 16-byte-aligned frames, 2K <= 224 (Z accumulators and two
+    // the second half of a row), 16-byte-aligned frames, 2K <= 224 (Z accumulators and three
     // A stages in 512 TMEM columns)
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const CUtensorMap *vmap = t.n1 > 0 ? tc_vmap_binmajor(b, bf) : nullptr;
@@ -400,19 +413,24 @@ int launch_svd_proj_tma(const sp_basis *b, const void *frames, int T, int prec, 
     p.a_col0 = p.n_zbuf == 2 ? p.z_cols + zw : zw;
     if (p.a_col0 + kGroups * kAStageCols > 512) return SP_ENOTIMPL;
     p.v_stage_bytes = 3 * t.n1 * 128;
-    const int fixed = 2 * p.v_stage_bytes + 256 + 1024;   // V stages, barriers, alignment slack
+    // shared memory (227 KB): three V stages and three raw slots of one chunk where they fit
+    // (V's L2 latency is the longer one), else two V stages with two slots of two chunks or three
+    // of one chunk
     const int slot2 = kTileRows * (64 * 2 + 16), slot1 = kTileRows * (64 + 16);
-    if (fixed + 2 * slot2 <= 232448) {
-        p.cpr = 2;
-        p.n_raw = 2;
-    } else {
-        p.cpr = 1;
-        p.n_raw = std::min(4, (232448 - fixed) / slot1);
-        if (p.n_raw < 3) return SP_ENOTIMPL;
+    const int over = 256 + 1024;   // barriers, alignment slack
+    int nv = 3, cpr = 1, n_raw = 3;
+    if (3 * p.v_stage_bytes + 3 * slot1 + over > 232448) {
+        nv = 2;
+        if (2 * p.v_stage_bytes + 2 * slot2 + over <= 232448) {
+            cpr = 2;
+            n_raw = 2;
+        } else if (2 * p.v_stage_bytes + 3 * slot1 + over > 232448) {
+            return SP_ENOTIMPL;
+        }
     }
-    p.slot_bytes = p.cpr == 2 ? slot2 : slot1;
-    p.e0_bytes = kTileRows * 32 * p.cpr;
-    p.n_raw_loads = (p.n_chunks + p.cpr - 1) / p.cpr;
+    p.slot_bytes = cpr == 2 ? slot2 : slot1;
+    p.e0_bytes = kTileRows * 32 * cpr;
+    p.n_raw_loads = (p.n_chunks + cpr - 1) / cpr;
     p.inv_vscale = 1.f / b->v_scale;
     p.z_out = (float2 *)z_out;
     p.zn2_out = zn2_out;
@@ -422,11 +440,14 @@ int launch_svd_proj_tma(const sp_basis *b, const void *frames, int T, int prec, 
     const uint64_t rows_all = ((uint64_t)T * kM + 1) / 2, rows_full = (uint64_t)T * kM / 2;
     const uint64_t pitch = (uint64_t)16 * B;
     CUtensorMap m0, m1;   // (T >= 1 gives at least 3 full rows)
-    SP_TRY(encode_tmap_f32_2d(&m0, frames, 2 * (uint64_t)B, rows_all, pitch, 8 * p.cpr, kBoxRows));
+    SP_TRY(encode_tmap_f32_2d(&m0, frames, 2 * (uint64_t)B, rows_all, pitch, 8 * cpr, kBoxRows));
     SP_TRY(encode_tmap_f32_2d(&m1, static_cast<const char *>(frames) + (size_t)(B - 1) * 8, 2 * (uint64_t)(B + 1),
-                              rows_full, pitch, 8 * p.cpr + 4, kBoxRows));
-    const int smem = fixed + p.n_raw * p.slot_bytes;
-    auto kern = bf ? svd_proj_tma_kernel<1> : svd_proj_tma_kernel<0>;
+                              rows_full, pitch, 8 * cpr + 4, kBoxRows));
+    const int smem = nv * p.v_stage_bytes + n_raw * p.slot_bytes + over;
+    using Kern = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, Params);
+    const Kern kern = nv == 3   ? (bf ? svd_proj_tma_kernel<1, 1, 3, 3> : svd_proj_tma_kernel<0, 1, 3, 3>)
+                      : cpr == 2 ? (bf ? svd_proj_tma_kernel<1, 2, 2, 2> : svd_proj_tma_kernel<0, 2, 2, 2>)
+                                 : (bf ? svd_proj_tma_kernel<1, 1, 3, 2> : svd_proj_tma_kernel<0, 1, 3, 2>);
     SP_TRY(ensure_max_smem((const void *)kern));
     const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
     kern<<<grid, kThreads, smem, s>>>(*vmap, m0, m1, p);
