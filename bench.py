@@ -43,11 +43,11 @@ METRIC = "localized frames/s at >=99.5% argmax agreement vs FP64 oracle"
 UNIT = "frames/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes read + written per frame by svd_proj_kernel, from one ncu capture of this
-# version of the kernel on 19,456 frames of the same workload (311.0 MB / 19,456), scaled to
-# a launch by the frame count (traffic grows in proportion to frames).  Set to None when the
-# kernel changes until it is captured again.
-TRAFFIC_PER_FRAME = 15985.0
+# DRAM bytes read + written per frame by the dominant kernel (svd_proj_tma_kernel), from one
+# ncu capture of this version of the kernel on 19,456 frames of the same workload, scaled to a
+# launch by the frame count (traffic grows in proportion to frames).  None until captured.
+TRAFFIC_PER_FRAME = 16121.7     # 313,662,976 B / 19,456 frames (read 307.7 MB, write 5.9 MB)
+DOMINANT_KERNEL = "svd_proj_tma_kernel"
 
 
 def _peaks():
@@ -120,8 +120,48 @@ class Clocks:
         return out
 
 
+def _oracle_block(args):
+    """One process's share of the FP64 oracle sample: PHAT, Z = V^H X, Re{D Z}, the argmax and
+    online step 4 (Algorithm 1) for a block of frames.  Returns (idx, Y)."""
+    import oracle as O
+    fr, V, D, tau, N = args
+    X = O.phat(fr)
+    Y = O.svd_scores(D, O.project(V, X))
+    idx, _ = O.argmax_lowest(Y)
+    O.score_row(tau, idx, X, N)
+    return idx, Y
+
+
+def _oracle_step4(args):
+    """Online step 4 of the oracle for given indices (error statistics, not timed)."""
+    import oracle as O
+    fr, tau, idx, N = args
+    return O.score_row(tau, idx, O.phat(fr), N)
+
+
+def _noop(_):
+    return 0
+
+
+_POOL = None
+
+
+def oracle_pool():
+    """A pool of spawned processes, one per host core the job may use, each with one BLAS thread:
+    the oracle's per-frame work runs on every core (frames are independent)."""
+    global _POOL
+    if _POOL is None:
+        import multiprocessing as mp
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        _POOL = mp.get_context("spawn").Pool(_cores())
+        _POOL.map(_noop, range(2 * _cores()))   # start every worker before any timing
+    return _POOL
+
+
 def oracle_sample(wl, n_frames: int, seed: int = 7):
-    """FP64 oracle on a bounded sample of the workload: returns (frames/s, cores, sel, idx_ref, Y, cls)."""
+    """FP64 oracle on a bounded sample of the workload, the frames split over every host core:
+    returns (frames/s, seconds, sel, idx_ref, Y, cls)."""
     import oracle as O
     tau = O.tdoa_farfield(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"])
     W = O.steering(tau, wl["N"])
@@ -129,14 +169,23 @@ def oracle_sample(wl, n_frames: int, seed: int = 7):
     rng = np.random.default_rng(seed)
     sel = np.sort(rng.choice(wl["frames"].shape[0], n_frames, replace=False))
     fr = wl["frames"][sel]
+    pool = oracle_pool()
+    blocks = np.array_split(np.arange(n_frames), _cores())
+    args = [(fr[b], ob["V"], ob["D"], tau, wl["N"]) for b in blocks if len(b)]
     t0 = time.perf_counter()
-    X = O.phat(fr)
-    Y = O.svd_scores(ob["D"], O.project(ob["V"], X))
-    idx, _ = O.argmax_lowest(Y)
-    O.score_row(tau, idx, X, wl["N"])
+    res = pool.map(_oracle_block, args)
     dt = time.perf_counter() - t0
-    oracle_sample.last = dict(tau=tau, X=X, L=W.shape[1])   # for error statistics (untimed)
+    idx = np.concatenate([r[0] for r in res])
+    Y = np.concatenate([r[1] for r in res])
+    oracle_sample.last = dict(tau=tau, fr=fr, L=W.shape[1], blocks=[b for b in blocks if len(b)])
     return n_frames / dt, dt, sel, idx, Y, O.direction_classes(tau)
+
+
+def oracle_step4(gi, N):
+    """The oracle's online step-4 scores of the last sample for the indices gi (untimed)."""
+    last = oracle_sample.last
+    res = oracle_pool().map(_oracle_step4, [(last["fr"][b], last["tau"], gi[b], N) for b in last["blocks"]])
+    return np.concatenate(res)
 
 
 def arm_config(K: int, T: int) -> dict:
@@ -188,8 +237,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": arm_config(K, args.frames),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-                             "sample": f"{n} frames per step (FP64 on the host cores) drawn from an 8192-frame "
-                                       "batch of the workload"},
+                             "sample": f"{n} frames per step drawn from an 8192-frame batch of the workload, FP64, "
+                                       f"split over {_cores()} spawned processes with one BLAS thread each"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -245,7 +294,7 @@ def bench_array3d(sp, I, torch, unique=C4_UNIQUE, repeat=C4_REPEAT):
         "svd_exhaustive_fp16_frames_per_s": T / t_exh * 1000,
         "svd_learned_fp16_frames_per_s": T / t_lrn * 1000,
         "svd_kdtree_fp16_frames_per_s": T / t_kd * 1000,
-        "ms_per_pass": {"svd_proj_kernel": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
+        "ms_per_pass": {"gemm1": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
                         "mlp_tc_kernel": t_mlp, "rescore_and_fallback_scan": t_lrn_ns - t_proj - t_mlp,
                         "step4_bulk_kernel": t_exh - t_exh_ns, "kdtree": t_kd - (t_exh - t_exh_ns) - t_proj},
         "learned": {"n_top": LEARNED_N_TOP, "theta": LEARNED_THETA, "cells": 642, "hidden": [256, 256],
@@ -307,7 +356,7 @@ def bench_c5(sp, I, torch):
                     f"-5..20 dB (no reverberation)",
         "svd_exhaustive_fp16_frames_per_s": T / t_exh * 1000,
         "svd_learned_fp16_frames_per_s": T / t_lrn * 1000,
-        "ms_per_pass": {"svd_proj_kernel": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
+        "ms_per_pass": {"gemm1": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
                         "step4": t_exh - t_exh_ns, "learned_total": t_lrn},
         "gemm1_hbm_GBps": 8 * 16 * 513 * T / (t_proj * 1e-3) / 1e9,
         "fp16_agreement_vs_fp32_path": float((ex16 == ex32).float().mean()),
@@ -462,7 +511,7 @@ def main():
     sp.check_status()
 
     # per-kernel durations on the launching stream: the dominant kernel (fused PHAT + GEMM1,
-    # svd_proj_kernel) alone through sp_project, then + the scan, then + online step 4
+    # svd_proj_tma_kernel) alone through sp_project, then + the scan, then + online step 4
     zbuf = torch.empty((T, b.K), dtype=torch.complex64, device="cuda")
     kout = (idx, None, proj)
 
@@ -520,7 +569,7 @@ def main():
         last = oracle_sample.last
         Lr = float(last["L"])
         proj_err = float(np.max(np.abs(proj.cpu().numpy()[sel] - Y[np.arange(len(sel)), gi]))) / Lr
-        s4_err = float(np.max(np.abs(score.cpu().numpy()[sel] - O.score_row(last["tau"], gi, last["X"], wl["N"])))) / Lr
+        s4_err = float(np.max(np.abs(score.cpu().numpy()[sel] - oracle_step4(gi, wl["N"])))) / Lr
         if not args.no_extras:
             # plain FP32 SRP-PHAT (the reference form) and the other precisions, same frames
             def rate_of(fn, n):
@@ -535,15 +584,14 @@ def main():
                 return T * n / (a.elapsed_time(z) / 1000)
             extras["srp_fp32_frames_per_s"] = rate_of(lambda: sp.localize_srp(st, frames), 2)
             # plain SRP-PHAT is FP32-ALU bound: 4 Q L flops per frame (Eq. 9) against the FP32 FMA
-            # peak from the unit counts (128 FP32 lanes per SM, 2 flops per FMA) and the SM clock
+            # rate measured on this GPU by the library's own microbenchmark (sp_fp32_fma_peak)
+            alu_peak = sp.fp32_fma_peak()
             sm_count = torch.cuda.get_device_properties(0).multi_processor_count
-            sm_mhz = clocks_sm_mhz(clk) or 2070.0
-            alu_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
             srp_tflops = extras["srp_fp32_frames_per_s"] * 4.0 * st.Q * st.L / 1e12
             extras["srp_fp32_roofline"] = {"bound": "alu", "achieved": srp_tflops, "peak": alu_peak,
                                            "unit": "TFLOP/s", "frac": srp_tflops / alu_peak,
-                                           "peak_source": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 flops x "
-                                                          f"{sm_mhz:.0f} MHz (median SM clock of the timed region)"}
+                                           "peak_source": "measured: sp_fp32_fma_peak (independent FMA chains "
+                                                          f"on all {sm_count} SMs, CUDA events)"}
             extras["svd_fp32_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", "fp32"), 3)
             other = "bf16" if args.prec == "fp16" else "fp16"
             extras[f"svd_{other}_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", other), 5)
@@ -566,12 +614,13 @@ def main():
             "gpu_launches": 5 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": TRAFFIC_PER_FRAME and TRAFFIC_PER_FRAME * T,
-                         "kernel": "svd_proj_kernel", "kernel_ms": k_ms, "peak_source": peak_kind,
+                         "kernel": DOMINANT_KERNEL, "kernel_ms": k_ms, "peak_source": peak_kind,
                          "algorithmic_bytes_per_frame": per_frame_bytes},
-            "kernel_ms": {"svd_proj_kernel": k_ms, "svd_scan_kernel": scan_ms, "step4_bulk_kernel": step4_ms},
+            "kernel_ms": {DOMINANT_KERNEL: k_ms, "svd_scan_kernel": scan_ms, "step4_bulk_kernel": step4_ms},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-                             "sample": "2048 frames of the same workload (PHAT, Z = V^H X, Re{D Z} argmax, "
-                                       "online step 4 in FP64 numpy)"},
+                             "sample": f"2048 frames of the same workload (PHAT, Z = V^H X, Re{{D Z}} argmax, "
+                                       f"online step 4 in FP64 numpy), split over {_cores()} spawned processes "
+                                       "with one BLAS thread each"},
             "e2e": {"value": T * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T * frame_bytes,
                     "d2h_bytes_per_step": T * 12, "host_to_device_copy_GBps": h2d_gbs},
             "clocks": clk,

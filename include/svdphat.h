@@ -282,6 +282,12 @@ int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, int T, sp_pre
  * (SP_ETIMEOUT if a bounded wait gave up), clearing it. */
 int sp_check_status(void *stream);
 
+/* Measurement aid (the paper has no counterpart): the FP32 fused multiply-add rate of the
+ * current device in TFLOP/s (2 flops per FMA), from a kernel of independent FMA chains on
+ * every SM, timed with CUDA events.  It is the denominator of the plain FP32 SRP-PHAT roofline
+ * (Eq. 9 costs 4 Q L flops per frame).  Synchronous; allocates 2 KB of device memory. */
+int sp_fp32_fma_peak(double *tflops);
+
 /* For tests: set the iteration budget of every bounded device wait (0 = default).
  * A budget of 1 makes waits give up at once, which exercises SP_ETIMEOUT. */
 int sp_set_wait_budget(long long iterations);

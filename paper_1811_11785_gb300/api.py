@@ -85,6 +85,7 @@ _SIGS = {
     "sp_localize_learned": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp, _vp, _vp, _vp,
                              _vp], ctypes.c_int),
     "sp_set_wait_budget": ([ctypes.c_longlong], ctypes.c_int),
+    "sp_fp32_fma_peak": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
 
@@ -386,6 +387,13 @@ def check_status():
 
 def set_wait_budget(cycles: int):
     _check("sp_set_wait_budget", lib().sp_set_wait_budget(int(cycles)))
+
+
+def fp32_fma_peak() -> float:
+    """sp_fp32_fma_peak: the measured FP32 FMA rate of the current device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check("sp_fp32_fma_peak", lib().sp_fp32_fma_peak(ctypes.byref(v)))
+    return v.value
 
 
 class Proposal:

@@ -56,3 +56,27 @@ def test_peaks_measured_and_fallback(tmp_path, monkeypatch):
     assert bench._peaks() == (6686.8, "measured")
     monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "absent.json"))
     assert bench._peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
+
+
+def test_parallel_oracle_sample_matches_the_serial_oracle():
+    """The CPU baseline splits the oracle's frames over spawned processes; the per-frame results
+    (argmax and scores) are those of the oracle run in one process."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1811_11785_gb300 import inputs as I
+    rng = np.random.default_rng(3)
+    mic = I.array_3d()
+    dirs = I.icosphere(2)
+    src = I.random_directions(rng, 40)[:, None, :]
+    fr = I.plane_wave_frames(rng, mic, 40, 64, 16000.0, 343.0, src, np.full(40, 10.0), "white")
+    wl = dict(mic_xyz=mic, dirs=dirs, fs=16000.0, c=343.0, N=64, delta=1e-5, frames=fr)
+    rate, dt, sel, idx, Y, cls = bench.oracle_sample(wl, 24, seed=5)
+    assert rate > 0 and len(sel) == 24
+    tau = O.tdoa_farfield(mic, dirs, 16000.0, 343.0)
+    ob = O.svd_basis(O.steering(tau, 64), 1e-5)
+    Yser = O.svd_scores(ob["D"], O.project(ob["V"], O.phat(fr[sel])))
+    assert np.max(np.abs(Y - Yser)) <= 1e-9 * tau.shape[1] * 33
+    assert np.array_equal(idx, O.argmax_lowest(Yser)[0])
+    s4 = bench.oracle_step4(idx, 64)
+    assert np.allclose(s4, O.score_row(tau, idx, O.phat(fr[sel]), 64), rtol=0, atol=1e-9)
