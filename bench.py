@@ -243,6 +243,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def kdtree_stats(sp, b, frames, torch, reps=3):
+    """The k-d tree search alone (sp_kdtree_search on sp_project's Z): mean nodes and leaf
+    buckets visited per query, and the bytes those visits read (leaf points 2K x 32 floats and
+    32 indices per bucket, 16 bytes per node, the query) per second of the search."""
+    Z = sp.project(b, frames, "fp16")
+    _, _, vis = sp.kdtree_search(b, Z)
+    torch.cuda.synchronize()
+    qps = _rate(lambda: sp.kdtree_search(b, Z, visits=False), reps, frames.shape[0], torch)
+    T = frames.shape[0]
+    v = vis.double().mean(dim=0).tolist()
+    K = b.K
+    bytes_per_q = v[1] * (2 * K * 32 * 4 + 32 * 4) + v[0] * 16 + 2 * K * 4
+    info = b.kdtree_info()
+    return {"queries_per_s": qps, "nodes_visited_mean": v[0], "leaf_buckets_visited_mean": v[1],
+            "leaf_buckets_total": (info["n_nodes"] + 1) // 2, "nodes_total": info["n_nodes"],
+            "points_visited_mean": 32 * v[1], "l2_read_GBps": bytes_per_q * qps / 1e9,
+            "bytes_read_per_query": bytes_per_q}
+
+
 C4_UNIQUE, C4_REPEAT = 32768, 32
 LEARNED_N_TOP, LEARNED_THETA = 8, 0.2
 
@@ -303,6 +322,7 @@ def bench_array3d(sp, I, torch, unique=C4_UNIQUE, repeat=C4_REPEAT):
                     "fallback_fraction": float(fb.float().mean()),
                     "agreement_vs_exhaustive": float((li == ex).float().mean())},
         "kdtree_agreement_vs_exhaustive": float((kd == ex).float().mean()),
+        "kdtree_search": kdtree_stats(sp, b, uniq, torch),
     }
     return out
 
@@ -596,6 +616,7 @@ def main():
             other = "bf16" if args.prec == "fp16" else "fp16"
             extras[f"svd_{other}_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", other), 5)
             extras["svd_kdtree_fp16_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_kdtree", "fp16"), 3)
+            extras["kdtree_search"] = kdtree_stats(sp, b, frames, torch)
             extras["array3d_q10242"] = bench_array3d(sp, I, torch, args.array3d_frames, C4_REPEAT)
             extras["batched_256_streams"] = bench_batched(sp, I, torch)
 

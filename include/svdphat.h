@@ -233,6 +233,18 @@ int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
 int sp_localize(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec,
                 int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * Online step 3 by the k-d tree (Eq. 15) on its own, from given projections: z_dev is device
+ * [T][K] complex64 (Z of Eq. 12, e.g. from sp_project).  idx_dev (device int32 [T]) receives
+ * the nearest normalised row D^_q to conj(Z / ||Z||) (exact search, FP32 distances, ties to
+ * the lowest index; -1 where ||Z|| is 0 or not finite) and proj_dev (device float [T] or NULL)
+ * the score Re{D^_idx Z^} = 1 - d^2 / 2.  visits_dev (device int32 [T][2] or NULL) receives per
+ * query the tree nodes and the leaf buckets (32 points each) the search visited.  The tree's
+ * nodes are read from shared memory when they fit in 96 KB.  Asynchronous on stream.
+ * --------------------------------------------------------------------------------- */
+int sp_kdtree_search(const sp_basis *b, const void *z_dev, int T, int32_t *idx_dev, float *proj_dev,
+                     int32_t *visits_dev, void *stream);
+
 /* Plain SRP-PHAT (Eq. 5, 6, 9) straight from a steering handle (no basis needed). */
 int sp_localize_srp(const sp_steering *st, const void *frames_dev, int T,
                     int32_t *idx_dev, float *score_dev, void *stream);

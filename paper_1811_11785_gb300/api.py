@@ -86,6 +86,7 @@ _SIGS = {
                              _vp], ctypes.c_int),
     "sp_set_wait_budget": ([ctypes.c_longlong], ctypes.c_int),
     "sp_fp32_fma_peak": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sp_kdtree_search": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -379,6 +380,21 @@ def localize_noalloc(basis: Basis, frames, prec="fp16", score=True, proj=True, o
     _check("sp_localize_noalloc", lib().sp_localize_noalloc(basis.handle, _ptr(frames), T, _prec(prec), _ptr(idx),
                                                             _ptr(sc), _ptr(pj), _stream()))
     return idx, sc, pj
+
+
+def kdtree_search(basis: Basis, Z, visits=True):
+    """sp_kdtree_search: the k-d tree search (Eq. 15) of given projections Z (device [T][K]
+    complex64).  Returns (idx, score, visits) with visits int32 [T][2] (nodes, leaf buckets)
+    or None."""
+    import torch
+    T = Z.shape[0]
+    assert Z.dtype == torch.complex64 and Z.is_contiguous() and Z.shape[1] == basis.K
+    idx = torch.empty(T, dtype=torch.int32, device=Z.device)
+    sc = torch.empty(T, dtype=torch.float32, device=Z.device)
+    vi = torch.empty((T, 2), dtype=torch.int32, device=Z.device) if visits else None
+    _check("sp_kdtree_search", lib().sp_kdtree_search(basis.handle, _ptr(Z), T, _ptr(idx), _ptr(sc), _ptr(vi),
+                                                      _stream()))
+    return idx, sc, vi
 
 
 def check_status():

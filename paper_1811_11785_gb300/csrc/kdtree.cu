@@ -123,120 +123,170 @@ int build_kdtree(sp_basis *b) {
     return SP_OK;
 }
 
-// One warp per query.  Shared memory per warp: the query (2K floats) and the stack.
-constexpr int KD_WARPS = 4;
+// One warp per query, KD_WARPS warps per CTA, CTAs striding over the queries.  Shared memory:
+// the tree's nodes (when they fit in kNodeSmem bytes; else they are read from global memory),
+// then per warp the query (2K floats) and the stack.  visits (optional, int32 [T][2]) receives,
+// per query, the nodes and the leaf buckets (32 points each) the search visited.
+constexpr int KD_WARPS = 8;
+constexpr int kNodeSmem = 96 * 1024;
 
 __global__ void __launch_bounds__(KD_WARPS * 32)
-    kdtree_kernel(const float2 *__restrict__ Z, int T, int K, const KdNode *__restrict__ nodes,
-                  const float *__restrict__ leaf_pts, const int32_t *__restrict__ leaf_ids,
-                  int32_t *__restrict__ idx_out, float *__restrict__ proj_out) {
-    extern __shared__ float smem[];
+    kdtree_kernel(const float2 *__restrict__ Z, int T, int K, const KdNode *__restrict__ nodes_g, int n_nodes,
+                  int nodes_in_smem, const float *__restrict__ leaf_pts, const int32_t *__restrict__ leaf_ids,
+                  int32_t *__restrict__ idx_out, float *__restrict__ proj_out, int32_t *__restrict__ visits) {
+    extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int dim = 2 * K;
-    float *qv = smem + warp * dim;
-    int *stk_node = reinterpret_cast<int *>(smem + KD_WARPS * dim) + warp * kMaxDepth;
-    float *stk_bound = reinterpret_cast<float *>(smem + KD_WARPS * dim + KD_WARPS * kMaxDepth) +
+    KdNode *nodes_s = reinterpret_cast<KdNode *>(smem);
+    const int node_floats = nodes_in_smem ? n_nodes * 4 : 0;
+    float *qv = smem + node_floats + warp * dim;
+    int *stk_node = reinterpret_cast<int *>(smem + node_floats + KD_WARPS * dim) + warp * kMaxDepth;
+    float *stk_bound = reinterpret_cast<float *>(smem + node_floats + KD_WARPS * dim + KD_WARPS * kMaxDepth) +
                        warp * kMaxDepth;
-    const long long t = (long long)blockIdx.x * KD_WARPS + warp;
-    if (t >= T) return;
-    // query: conj(Z / ||Z||) embedded as [Re, -Im]
-    float n2 = 0.f;
-    for (int k = lane; k < K; k += 32) {
-        const float2 z = Z[(size_t)t * K + k];
-        n2 += z.x * z.x + z.y * z.y;
+    if (nodes_in_smem) {
+        for (int i = threadIdx.x; i < n_nodes; i += blockDim.x) nodes_s[i] = nodes_g[i];
+        __syncthreads();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-    if (!(n2 > 0.f) || !isfinite(n2)) {
-        if (lane == 0) {
-            idx_out[t] = -1;
-            if (proj_out) proj_out[t] = __int_as_float(0x7fc00000);
+    const KdNode *nodes = nodes_in_smem ? nodes_s : nodes_g;
+    for (long long t = (long long)blockIdx.x * KD_WARPS + warp; t < T; t += (long long)gridDim.x * KD_WARPS) {
+        // query: conj(Z / ||Z||) embedded as [Re, -Im]
+        float n2 = 0.f;
+        for (int k = lane; k < K; k += 32) {
+            const float2 z = Z[(size_t)t * K + k];
+            n2 += z.x * z.x + z.y * z.y;
         }
-        return;
-    }
-    const float inv = rsqrtf(n2);
-    for (int k = lane; k < K; k += 32) {
-        const float2 z = Z[(size_t)t * K + k];
-        qv[k] = z.x * inv;
-        qv[K + k] = -z.y * inv;
-    }
-    __syncwarp();
-    float best_d = __int_as_float(0x7f800000);
-    int best_id = 0x7fffffff;
-    int sp = 0;
-    if (lane == 0) {
-        stk_node[0] = 0;
-        stk_bound[0] = 0.f;
-    }
-    sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-        --sp;
-        int node = stk_node[sp];
-        float bound = stk_bound[sp];
-        __syncwarp();
-        if (bound > best_d) continue;
-        KdNode nd = nodes[node];
-        while (nd.dim >= 0) {
-            const float diff = qv[nd.dim] - nd.split;
-            const int near_c = diff < 0.f ? node + 1 : nd.right;
-            const int far_c = diff < 0.f ? nd.right : node + 1;
-            const float fb = fmaxf(bound, diff * diff);
-            if (fb <= best_d && sp < kMaxDepth) {
-                if (lane == 0) {
-                    stk_node[sp] = far_c;
-                    stk_bound[sp] = fb;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        if (!(n2 > 0.f) || !isfinite(n2)) {
+            if (lane == 0) {
+                idx_out[t] = -1;
+                if (proj_out) proj_out[t] = __int_as_float(0x7fc00000);
+                if (visits) {
+                    visits[2 * t] = 0;
+                    visits[2 * t + 1] = 0;
                 }
-                ++sp;
             }
-            node = near_c;
-            nd = nodes[node];
+            continue;
+        }
+        const float inv = rsqrtf(n2);
+        __syncwarp();   // the previous query's reads of qv are done
+        for (int k = lane; k < K; k += 32) {
+            const float2 z = Z[(size_t)t * K + k];
+            qv[k] = z.x * inv;
+            qv[K + k] = -z.y * inv;
         }
         __syncwarp();
-        // leaf bucket: lane j scores point j
-        const int bucket = nd.right;
-        const float *pb = leaf_pts + (size_t)bucket * dim * 32 + lane;
-        float d2 = 0.f;
-        for (int d = 0; d < dim; ++d) {
-            const float df = qv[d] - pb[(size_t)d * 32];
-            d2 = fmaf(df, df, d2);
+        float best_d = __int_as_float(0x7f800000);
+        int best_id = 0x7fffffff;
+        int n_nodes_seen = 0, n_leaves = 0;
+        if (lane == 0) {
+            stk_node[0] = 0;
+            stk_bound[0] = 0.f;
         }
-        int id = leaf_ids[(size_t)bucket * 32 + lane];
-        if (id < 0) {
-            d2 = __int_as_float(0x7f800000);
-            id = 0x7fffffff;
-        }
+        int sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+            --sp;
+            int node = stk_node[sp];
+            float bound = stk_bound[sp];
+            __syncwarp();
+            if (bound > best_d) continue;
+            KdNode nd = nodes[node];
+            ++n_nodes_seen;
+            while (nd.dim >= 0) {
+                const float diff = qv[nd.dim] - nd.split;
+                const int near_c = diff < 0.f ? node + 1 : nd.right;
+                const int far_c = diff < 0.f ? nd.right : node + 1;
+                const float fb = fmaxf(bound, diff * diff);
+                if (fb <= best_d && sp < kMaxDepth) {
+                    if (lane == 0) {
+                        stk_node[sp] = far_c;
+                        stk_bound[sp] = fb;
+                    }
+                    ++sp;
+                }
+                node = near_c;
+                nd = nodes[node];
+                ++n_nodes_seen;
+            }
+            __syncwarp();
+            // leaf bucket: lane j scores point j
+            ++n_leaves;
+            const int bucket = nd.right;
+            const float *pb = leaf_pts + (size_t)bucket * dim * 32 + lane;
+            float d2 = 0.f;
+            for (int d = 0; d < dim; ++d) {
+                const float df = qv[d] - pb[(size_t)d * 32];
+                d2 = fmaf(df, df, d2);
+            }
+            int id = leaf_ids[(size_t)bucket * 32 + lane];
+            if (id < 0) {
+                d2 = __int_as_float(0x7f800000);
+                id = 0x7fffffff;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float od = __shfl_xor_sync(0xffffffffu, d2, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, id, o);
-            if (od < d2 || (od == d2 && oi < id)) {
-                d2 = od;
-                id = oi;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, d2, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, id, o);
+                if (od < d2 || (od == d2 && oi < id)) {
+                    d2 = od;
+                    id = oi;
+                }
+            }
+            if (d2 < best_d || (d2 == best_d && id < best_id)) {
+                best_d = d2;
+                best_id = id;
             }
         }
-        if (d2 < best_d || (d2 == best_d && id < best_id)) {
-            best_d = d2;
-            best_id = id;
+        if (lane == 0) {
+            idx_out[t] = best_id == 0x7fffffff ? -1 : best_id;
+            if (proj_out) proj_out[t] = 1.f - 0.5f * best_d;
+            if (visits) {
+                visits[2 * t] = n_nodes_seen;
+                visits[2 * t + 1] = n_leaves;
+            }
         }
-    }
-    if (lane == 0) {
-        idx_out[t] = best_id == 0x7fffffff ? -1 : best_id;
-        if (proj_out) proj_out[t] = 1.f - 0.5f * best_d;
     }
 }
 
-int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
-                  cudaStream_t s) {
+int launch_kdtree_stats(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj, int32_t *visits,
+                        cudaStream_t s) {
     if (T == 0) return SP_OK;
     const int dim = 2 * b->K;
-    const size_t smem = (size_t)KD_WARPS * dim * 4 + (size_t)KD_WARPS * kMaxDepth * 8;
-    const long long blocks = ((long long)T + KD_WARPS - 1) / KD_WARPS;
-    kdtree_kernel<<<(unsigned)blocks, KD_WARPS * 32, smem, s>>>(
-        (const float2 *)Z, T, b->K, b->nodes.as<KdNode>(), b->leaf_pts.as<float>(),
-        b->leaf_ids.as<int32_t>(), idx, proj);
+    const size_t node_bytes = (size_t)b->n_nodes * sizeof(KdNode);
+    const int in_smem = node_bytes <= (size_t)kNodeSmem ? 1 : 0;
+    const size_t smem = (in_smem ? node_bytes : 0) + (size_t)KD_WARPS * dim * 4 + (size_t)KD_WARPS * kMaxDepth * 8;
+    SP_CHECK(smem <= 232448, SP_ENOTIMPL, "k-d tree: shared-memory plan exceeds 227 KB");
+    if (smem > 48 * 1024) SP_TRY(ensure_max_smem((const void *)kdtree_kernel));
+    const long long need = ((long long)T + KD_WARPS - 1) / KD_WARPS;
+    const unsigned grid = (unsigned)std::min<long long>(need, 8LL * num_sms());
+    kdtree_kernel<<<grid, KD_WARPS * 32, smem, s>>>((const float2 *)Z, T, b->K, b->nodes.as<KdNode>(), b->n_nodes,
+                                                     in_smem, b->leaf_pts.as<float>(), b->leaf_ids.as<int32_t>(),
+                                                     idx, proj, visits);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
 
+int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj, cudaStream_t s) {
+    return launch_kdtree_stats(b, Z, T, idx, proj, nullptr, s);
+}
+
 }  // namespace sp
+
+using namespace sp;
+
+extern "C" int sp_kdtree_search(const sp_basis *b, const void *z_dev, int T, int32_t *idx_dev, float *proj_dev,
+                                int32_t *visits_dev, void *stream) {
+    SP_CHECK(b, SP_EINVAL, "sp_kdtree_search: null basis");
+    SP_CHECK(T >= 0 && T <= (1 << 28), SP_EINVAL, "sp_kdtree_search: T out of range");
+    if (T == 0) return SP_OK;
+    SP_CHECK(z_dev && (reinterpret_cast<uintptr_t>(z_dev) & 7) == 0, SP_EINVAL,
+             "sp_kdtree_search: z_dev NULL or misaligned");
+    SP_CHECK(idx_dev && (reinterpret_cast<uintptr_t>(idx_dev) & 3) == 0, SP_EINVAL,
+             "sp_kdtree_search: idx_dev NULL or misaligned");
+    SP_CHECK(!proj_dev || (reinterpret_cast<uintptr_t>(proj_dev) & 3) == 0, SP_EINVAL,
+             "sp_kdtree_search: proj_dev misaligned");
+    SP_CHECK(!visits_dev || (reinterpret_cast<uintptr_t>(visits_dev) & 3) == 0, SP_EINVAL,
+             "sp_kdtree_search: visits_dev misaligned");
+    return launch_kdtree_stats(b, z_dev, T, idx_dev, proj_dev, visits_dev, (cudaStream_t)stream);
+}

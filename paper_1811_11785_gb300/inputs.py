@@ -371,3 +371,32 @@ def batched_streams(n: int, M_range=(4, 16), Q_choices=(642, 2562, 10242), N_cho
         out.append(dict(mic_xyz=mic, dirs=icosphere(icosphere_level_for(Q)), N=N, fs=16000.0, c=343.0,
                         delta=1e-5, frames=frames, src_dirs=src, snr_db=snr))
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Time-domain signals for the STFT front end
+# --------------------------------------------------------------------------------------
+
+def time_signals(rng: np.random.Generator, mic_xyz: np.ndarray, S: int, fs: float, c: float,
+                 src_dir: np.ndarray, snr_db: float) -> np.ndarray:
+    """``[M][S]`` float32 samples: one white Gaussian source from direction ``src_dir`` (unit
+    vector), microphone m receiving it advanced by fs/c r_m . u samples (a fractional, circular
+    delay applied as a phase ramp over the whole signal's FFT), plus independent white noise at
+    ``snr_db`` (microphone-averaged signal power over noise power)."""
+    mic_xyz = np.asarray(mic_xyz, dtype=np.float64)
+    u = np.asarray(src_dir, dtype=np.float64)
+    u = u / np.linalg.norm(u)
+    s = rng.standard_normal(S)
+    Sf = np.fft.rfft(s)
+    k = np.arange(Sf.shape[0])
+    d = fs / c * (mic_xyz @ u)                       # advance of each microphone in samples
+    x = np.fft.irfft(Sf[None, :] * np.exp(2j * np.pi * k[None, :] * d[:, None] / S), n=S, axis=1)
+    p_sig = np.mean(x ** 2)
+    noise = rng.standard_normal(x.shape) * np.sqrt(p_sig / 10.0 ** (snr_db / 10.0))
+    return (x + noise).astype(np.float32)
+
+
+def random_mask(rng: np.random.Generator, T: int, B: int, keep: float) -> np.ndarray:
+    """A binary time-frequency mask ``[T][B]`` (uint8, 1 = keep) with each bin kept with
+    probability ``keep``."""
+    return (rng.random((T, B)) < keep).astype(np.uint8)

@@ -260,6 +260,25 @@ def test_localize_kdtree(name, T, prec):
     assert np.max(np.abs(proj.cpu().numpy() - (1 - d2 / 2))) < 1e-4
 
 
+@pytest.mark.parametrize("name,T", [("planar_q2562", 777), ("array3d_q10242", 256)])
+def test_kdtree_search_visits(name, T):
+    """The step-level tree search (Eq. 15) on sp_project's Z gives sp_localize's k-d tree result,
+    and its visit counters are consistent with the tree: at least one root-to-leaf path (depth
+    nodes, one bucket) per query, at most every node and bucket."""
+    d = _setup(name, T)
+    b = d["b"]
+    Z = sp.project(b, d["frames"], "fp16")
+    idx, score, visits = sp.kdtree_search(b, Z)
+    ref, _, pref = sp.localize(b, d["frames"], "svd_kdtree", "fp16", score=False)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, ref) and torch.equal(score, pref)
+    info = b.kdtree_info()
+    n_leaves = (info["n_nodes"] + 1) // 2
+    v = visits.cpu().numpy()
+    assert np.all(v[:, 0] >= info["depth"] - 1) and np.all(v[:, 0] <= info["n_nodes"])
+    assert np.all(v[:, 1] >= 1) and np.all(v[:, 1] <= n_leaves)
+
+
 def test_tree_shape():
     d = _setup("planar_q2562", 777)
     info = d["b"].kdtree_info()
