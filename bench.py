@@ -388,6 +388,93 @@ def bench_c5(sp, I, torch):
     }
 
 
+def bench_samples(sp, I, torch, T=65536, seg_frames=1024):
+    """Localisation from time samples (Section 2's STFT front end, then Algorithm 1's online
+    path): the planar 7-microphone array, Q = 2562, N = 512, hop 256, T frames from
+    T * 256 + 256 samples per microphone (float32, channel rows), one white source per segment of
+    seg_frames frames from a seeded direction, white noise at 10 dB.  Reports frames/s through
+    sp_localize_samples (algorithmic bytes: the 7 x 256 new samples of a frame, 7,168 B), the
+    STFT kernel alone against the HBM peak (reads 7,168 B, writes 14,392 B per frame), and the
+    same with a binary mask keeping half the bins."""
+    wl = I.workload(WORKLOAD, T=64)
+    N, hop = 512, 256
+    st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], N)
+    b = sp.svd_reduce(st, wl["delta"])
+    rng = np.random.default_rng(I.SEED_BASE + 80)
+    seg = seg_frames * hop
+    n_seg = (T * hop + hop + seg - 1) // seg
+    x = np.concatenate([I.time_signals(rng, wl["mic_xyz"], seg, wl["fs"], wl["c"], u, 10.0)
+                        for u in I.random_directions(rng, n_seg)], axis=1)[:, :T * hop + hop]
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    del x
+    assert sp.n_frames(xt.shape[1], N, hop) == T
+    out = (torch.empty(T, dtype=torch.int32, device="cuda"), torch.empty(T, dtype=torch.float32, device="cuda"),
+           torch.empty(T, dtype=torch.float32, device="cuda"))
+    frames = torch.empty((T, 7, N // 2 + 1), dtype=torch.complex64, device="cuda")
+    mask = torch.from_numpy(I.random_mask(rng, T, N // 2 + 1, 0.5)).cuda()
+    peak, peak_kind = _peaks()
+
+    def stft_only():
+        rc = sp.lib().sp_stft(ctypes.c_void_p(xt.data_ptr()), 7, xt.shape[1], xt.stride(0), N, hop, None,
+                              ctypes.c_void_p(frames.data_ptr()), None,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, sp.lib().sp_last_error()
+
+    r_all = _rate(lambda: sp.localize_samples(b, xt, hop, "svd_exhaustive", "fp16", T=T, out=out), 10, T, torch)
+    r_mask = _rate(lambda: sp.localize_samples(b, xt, hop, "svd_exhaustive", "fp16", mask=mask, T=T, out=out), 10,
+                   T, torch)
+    r_stft = _rate(stft_only, 10, T, torch)
+    stft_gbs = r_stft * (7 * hop * 4 + 7 * (N // 2 + 1) * 8) / 1e9
+    return {"workload": f"planar_q2562 from time samples: 7 mics, N={N}, hop={hop}, K={b.K}, {T} frames "
+                        f"({T * hop + hop} samples per microphone, float32), one white source per {seg_frames} "
+                        "frames, white noise 10 dB",
+            "frames_per_s": r_all, "algorithmic_bytes_per_frame": 7 * hop * 4,
+            "sample_GBps": r_all * 7 * hop * 4 / 1e9,
+            "masked_half_bins_frames_per_s": r_mask,
+            "stft_kernel": {"frames_per_s": r_stft, "GBps": stft_gbs, "peak": peak, "peak_source": peak_kind,
+                            "frac": stft_gbs / peak,
+                            "bytes_per_frame": 7 * hop * 4 + 7 * (N // 2 + 1) * 8}}
+
+
+SWEEP_DELTAS = (1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1)
+
+
+def bench_delta_sweep(sp, I, torch, n_cfg=12, seconds=1.0):
+    """Section 4's experiment on synthetic rooms: for the 1-D, 2-D and 3-D arrays of Table 2
+    (Table 1: fs 16 kHz, c 343 m/s, N 256, hop 128, Q 2562), n_cfg shoebox configurations
+    (10 x 10 x 3 m, wall reflection coefficients U(0.2, 0.5), image method to 2 reflections, a
+    white-noise source, white noise at 0-30 dB; TIMIT is not available), each `seconds` of
+    audio through the STFT front end.  Per delta: K (Eq. 11), the gain Q/K, and Delta RMSE, the
+    mean over configurations of the energy-weighted DOA error (Eq. 20) of SVD-PHAT (FP32
+    exhaustive search) minus that of SRP-PHAT on the same frames."""
+    fs, c, N, hop = 16000.0, 343.0, 256, 128
+    dirs = I.icosphere(4)
+    arrays = {1: ("1-D linear", I.array_linear_1d()), 2: ("2-D planar", I.array_planar_2d_table()),
+              3: ("3-D", I.array_3d())}
+    out = {"workload": f"{n_cfg} shoebox rooms per array, {seconds:.1f} s of audio each, N={N}, hop={hop}, Q=2562",
+           "deltas": list(SWEEP_DELTAS)}
+    t0 = time.perf_counter()
+    for alpha, (name, mic) in arrays.items():
+        st = sp.build_steering(mic, dirs, fs, c, N, materialize_w=True)
+        bases = [sp.svd_reduce(st, d) for d in SWEEP_DELTAS]
+        rng = np.random.default_rng(I.SEED_BASE + 90 + alpha)
+        r_srp, r_svd = [], [[] for _ in SWEEP_DELTAS]
+        for _ in range(n_cfg):
+            x, s0, _, _ = I.room_signals(rng, mic, int(seconds * fs), fs, c)
+            frames = sp.stft(torch.from_numpy(x).cuda(), N, hop)
+            i0, y0 = sp.localize_srp(st, frames)
+            r_srp.append(sp.weighted_doa_error(st, i0, y0, s0, alpha))
+            for k, b in enumerate(bases):
+                i1, y1, _ = sp.localize(b, frames, "svd_exhaustive", "fp32")
+                r_svd[k].append(sp.weighted_doa_error(st, i1, y1, s0, alpha))
+        out[name] = {"K": [b.K for b in bases], "gain_Q_over_K": [2562 / b.K for b in bases],
+                     "rmse_srp_mean": float(np.mean(r_srp)),
+                     "rmse_svd_mean": [float(np.mean(r)) for r in r_svd],
+                     "delta_rmse": [float(np.mean(r) - np.mean(r_srp)) for r in r_svd]}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
 N_STREAMS, N_CONFIGS = 256, 16
 
 
@@ -453,7 +540,7 @@ def main():
     ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16"])
     ap.add_argument("--frames", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the SRP / precision comparison lines")
-    ap.add_argument("--only", choices=["array3d", "batched", "c5"], default=None,
+    ap.add_argument("--only", choices=["array3d", "batched", "c5", "samples", "sweep"], default=None,
                     help="run only one extra section and print its JSON (profiling runs)")
     ap.add_argument("--array3d-frames", type=int, default=C4_UNIQUE,
                     help="unique frames of the 3-D array section (repeated to 2^20 unless --only)")
@@ -481,6 +568,10 @@ def main():
             print(json.dumps(bench_array3d(sp, I, torch, args.array3d_frames, 1)), flush=True)
         elif args.only == "c5":
             print(json.dumps(bench_c5(sp, I, torch)), flush=True)
+        elif args.only == "samples":
+            print(json.dumps(bench_samples(sp, I, torch)), flush=True)
+        elif args.only == "sweep":
+            print(json.dumps(bench_delta_sweep(sp, I, torch)), flush=True)
         else:
             print(json.dumps(bench_batched(sp, I, torch)), flush=True)
         return
@@ -617,6 +708,8 @@ def main():
             extras[f"svd_{other}_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_exhaustive", other), 5)
             extras["svd_kdtree_fp16_frames_per_s"] = rate_of(lambda: sp.localize(b, frames, "svd_kdtree", "fp16"), 3)
             extras["kdtree_search"] = kdtree_stats(sp, b, frames, torch)
+            extras["from_samples"] = bench_samples(sp, I, torch)
+            extras["delta_sweep"] = bench_delta_sweep(sp, I, torch)
             extras["array3d_q10242"] = bench_array3d(sp, I, torch, args.array3d_frames, C4_REPEAT)
             extras["batched_256_streams"] = bench_batched(sp, I, torch)
 

@@ -290,6 +290,51 @@ int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode 
 int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
                         int32_t *idx_dev, float *score_dev, float *proj_score_dev, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * The STFT front end of Section 2 (the expression X_m^l[k] that Eq. 3 starts from) and the
+ * binary time-frequency mask the paper's conclusion proposes.
+ *
+ * sp_stft: X_m^l[k] = sum_{n<N} w[n] x_m[l hop + n] exp(-2 pi i k n / N) for k = 0 .. N/2 and
+ * every whole frame l = 0 .. T-1, T = floor((n_samples - N) / hop) + 1 (0 when n_samples < N),
+ * with the sine window w[n] = sin(pi (n + 1/2) / N) and no normalisation.  FP32 arithmetic:
+ * an N/2-point complex FFT of the even/odd samples (radix-2, shared memory) and the real-input
+ * post-processing.
+ *   samples_dev: device float [M][ld] (channel rows, 4-byte aligned), n_samples <= ld per row.
+ *   N: power of two in [4, 8192]; hop >= 1.
+ *   mask_dev: device uint8 [T][N/2+1] or NULL; a bin whose mask is 0 is written as 0 for every
+ *     channel.  Under Eq. 3's zero rule such a bin contributes nothing to any cross spectrum,
+ *     so it drops out of Eq. 5, 9, 12, 14 and of online step 4.
+ *   frames_dev: device [T][M][N/2+1] complex64 (8-byte aligned), the layout sp_localize takes.
+ *   T_out (may be NULL) receives T.  Errors: SP_EINVAL (sizes, pointers), SP_ENOTIMPL (N).
+ * sp_apply_mask: out[l][m][k] = mask[l][k] ? frames[l][m][k] : 0 for STFT frames from elsewhere
+ *   ([T][M][B] complex64, 8-byte aligned; out may equal frames).
+ * sp_localize_samples: sp_stft of the first T frames into the basis's workspace (M and N of the
+ *   basis), then sp_localize of those frames; T <= the whole frames in the samples.  Outputs,
+ *   modes, precisions and errors as for sp_localize.  Asynchronous on stream.
+ * --------------------------------------------------------------------------------- */
+int sp_stft(const float *samples_dev, int M, long long n_samples, long long ld, int N, int hop,
+            const uint8_t *mask_dev, void *frames_dev, int *T_out, void *stream);
+int sp_apply_mask(const void *frames_dev, int T, int M, int B, const uint8_t *mask_dev, void *out_dev,
+                  void *stream);
+int sp_localize_samples(const sp_basis *b, const float *samples_dev, long long n_samples, long long ld, int hop,
+                        const uint8_t *mask_dev, int T, sp_mode mode, sp_prec prec, int32_t *idx_dev,
+                        float *score_dev, float *proj_score_dev, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * The energy-weighted DOA error of Section 4 (Eq. 16-20) for the T frames of one
+ * configuration: RMSE_alpha = || sum_l f_alpha(s_idx[l]) Y[l] / sum_l Y[l] - f_alpha(s0) ||_2,
+ * with s_idx[l] the unit direction of grid point idx[l] of st, Y = score_dev (the energy of the
+ * chosen direction, Algorithm 1's online step 4 as sp_localize writes it), and f_1 (arc, Eq. 16,
+ * 17), f_2 (upper hemisphere, Eq. 18), f_3 (identity, Eq. 19) for the 1-D, 2-D and 3-D arrays.
+ * Frames with idx < 0 or a non-finite Y are left out.  FP64 sums in a fixed order.
+ * idx_dev: device int32 [T]; score_dev: device float [T]; s0: host double [3], the true
+ * direction (need not be unit length); alpha in {1, 2, 3}; rmse_out: host double.
+ * Synchronous on stream (allocates 32 bytes of device memory).  Errors: SP_EINVAL (arguments,
+ * energies summing to zero), SP_ECUDA.
+ * --------------------------------------------------------------------------------- */
+int sp_weighted_doa_error(const sp_steering *st, const int32_t *idx_dev, const float *score_dev, int T,
+                          const double *s0, int alpha, double *rmse_out, void *stream);
+
 /* Synchronise stream and report a device-side failure recorded since the last call
  * (SP_ETIMEOUT if a bounded wait gave up), clearing it. */
 int sp_check_status(void *stream);

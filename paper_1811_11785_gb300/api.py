@@ -87,6 +87,13 @@ _SIGS = {
     "sp_set_wait_budget": ([ctypes.c_longlong], ctypes.c_int),
     "sp_fp32_fma_peak": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sp_kdtree_search": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "sp_stft": ([_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                 ctypes.POINTER(ctypes.c_int), _vp], ctypes.c_int),
+    "sp_apply_mask": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "sp_weighted_doa_error": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               _vp], ctypes.c_int),
+    "sp_localize_samples": ([_vp, _vp, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -395,6 +402,77 @@ def kdtree_search(basis: Basis, Z, visits=True):
     _check("sp_kdtree_search", lib().sp_kdtree_search(basis.handle, _ptr(Z), T, _ptr(idx), _ptr(sc), _ptr(vi),
                                                       _stream()))
     return idx, sc, vi
+
+
+def n_frames(n_samples: int, N: int, hop: int) -> int:
+    """Whole frames of N samples with hop `hop` in n_samples samples."""
+    return 0 if n_samples < N else (n_samples - N) // hop + 1
+
+
+def _samples(x):
+    import torch
+    assert x.is_cuda and x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1, \
+        "samples must be a CUDA float32 [M][S] tensor with contiguous rows"
+    return x
+
+
+def stft(samples, N: int, hop: int, mask=None):
+    """sp_stft: sine-window STFT (Section 2) of device samples [M][S] -> frames [T][M][N/2+1]
+    complex64; `mask` (uint8 [T][N/2+1], 0 = drop) zeroes bins."""
+    import torch
+    x = _samples(samples)
+    M, S = x.shape
+    T = n_frames(S, N, hop)
+    out = torch.empty((T, M, N // 2 + 1), dtype=torch.complex64, device=x.device)
+    t = ctypes.c_int()
+    _check("sp_stft", lib().sp_stft(_ptr(x), M, S, x.stride(0), N, hop, _ptr(mask), _ptr(out), ctypes.byref(t),
+                                    _stream()))
+    assert t.value == T
+    return out
+
+
+def apply_mask(frames, mask, out=None):
+    """sp_apply_mask: frames [T][M][B] complex64 with the bins of mask == 0 zeroed."""
+    import torch
+    T, M, B = frames.shape
+    assert mask.dtype == torch.uint8 and tuple(mask.shape) == (T, B)
+    out = torch.empty_like(frames) if out is None else out
+    _check("sp_apply_mask", lib().sp_apply_mask(_ptr(frames), T, M, B, _ptr(mask.contiguous()), _ptr(out), _stream()))
+    return out
+
+
+def localize_samples(basis: Basis, samples, hop: int, mode="svd_exhaustive", prec="fp16", mask=None, T=None,
+                     score=True, proj=True, out=None):
+    """sp_localize_samples: the STFT front end then sp_localize, from device samples [M][S]."""
+    import torch
+    x = _samples(samples)
+    M, S = x.shape
+    st = basis.steering
+    if T is None:
+        T = n_frames(S, st.N, hop)
+    if out is None:
+        idx = torch.empty(T, dtype=torch.int32, device=x.device)
+        sc = torch.empty(T, dtype=torch.float32, device=x.device) if score else None
+        pj = torch.empty(T, dtype=torch.float32, device=x.device) if proj else None
+    else:
+        idx, sc, pj = out
+    _check("sp_localize_samples", lib().sp_localize_samples(basis.handle, _ptr(x), S, x.stride(0), hop, _ptr(mask), T,
+                                                            _mode(mode), _prec(prec), _ptr(idx), _ptr(sc), _ptr(pj),
+                                                            _stream()))
+    return idx, sc, pj
+
+
+def weighted_doa_error(steering: Steering, idx, score, s0, alpha: int) -> float:
+    """sp_weighted_doa_error: Section 4's energy-weighted DOA error (Eq. 20) of one configuration."""
+    import torch
+    assert idx.dtype == torch.int32 and score.dtype == torch.float32 and idx.shape == score.shape
+    s0 = np.ascontiguousarray(s0, dtype=np.float64)
+    v = ctypes.c_double()
+    _check("sp_weighted_doa_error", lib().sp_weighted_doa_error(steering.handle, _ptr(idx.contiguous()),
+                                                                _ptr(score.contiguous()), idx.shape[0],
+                                                                s0.ctypes.data_as(ctypes.c_void_p), int(alpha),
+                                                                ctypes.byref(v), _stream()))
+    return v.value
 
 
 def check_status():

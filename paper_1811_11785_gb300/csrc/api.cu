@@ -455,6 +455,25 @@ int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode 
     return SP_OK;
 }
 
+int sp_localize_samples(const sp_basis *b, const float *samples_dev, long long n_samples, long long ld, int hop,
+                        const uint8_t *mask_dev, int T, sp_mode mode, sp_prec prec, int32_t *idx_dev,
+                        float *score_dev, float *proj_score_dev, void *stream) {
+    SP_CHECK(b, SP_EINVAL, "sp_localize_samples: null basis");
+    const sp_steering *st = b->st;
+    SP_TRY(check_stft_args(samples_dev, st->M, n_samples, ld, st->N, hop));
+    SP_CHECK(T >= 0 && T <= stft_frames(n_samples, st->N, hop), SP_EINVAL,
+             "sp_localize_samples: T exceeds the whole frames in the samples");
+    if (T == 0) return SP_OK;
+    SP_CHECK(idx_dev && aligned(idx_dev, 4), SP_EINVAL, "sp_localize_samples: idx_dev NULL or misaligned");
+    SP_CHECK(!score_dev || aligned(score_dev, 4), SP_EINVAL, "sp_localize_samples: score_dev misaligned");
+    SP_CHECK(!proj_score_dev || aligned(proj_score_dev, 4), SP_EINVAL,
+             "sp_localize_samples: proj_score_dev misaligned");
+    SP_TRY(b->fe_frames.reserve((size_t)T * st->M * st->B * 8));
+    cudaStream_t s = (cudaStream_t)stream;
+    SP_TRY(launch_stft(samples_dev, ld, st->M, st->N, hop, T, mask_dev, b->fe_frames.p, s));
+    return sp_localize(b, b->fe_frames.p, T, mode, prec, idx_dev, score_dev, proj_score_dev, stream);
+}
+
 int sp_check_status(void *stream) {
     int status = 0;
     SP_TRY(read_and_clear_device_status((cudaStream_t)stream, &status));

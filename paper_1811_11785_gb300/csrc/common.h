@@ -144,6 +144,7 @@ struct sp_basis {
     int n_nodes = 0, leaf_size = 32, depth = 0, n_slots = 0;
     mutable sp::DevBuf work;            // workspace for localize calls
     mutable sp::DevBuf stage[2];        // host-path staging
+    mutable sp::DevBuf fe_frames;       // STFT frames of sp_localize_samples
     mutable cudaStream_t copy_stream = nullptr;      // host-path copies
     mutable cudaEvent_t ev_loaded[2] = {nullptr, nullptr};
     mutable cudaEvent_t ev_free[2] = {nullptr, nullptr};
@@ -223,4 +224,9 @@ int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
 int check_localize_args(const sp_basis *b, const void *frames_dev, int T, const int32_t *idx_dev,
                         const float *score_dev, const float *proj_score_dev);
 int build_classes(sp_steering *st);   // rep_of / reps from the TDOA table (host)
+// STFT front end (Section 2): number of whole frames, argument checks, launch
+int stft_frames(long long n_samples, int N, int hop);
+int check_stft_args(const float *x, int M, long long n_samples, long long ld, int N, int hop);
+int launch_stft(const float *x, long long ld, int M, int N, int hop, int T, const uint8_t *mask, void *frames,
+                cudaStream_t s);
 }  // namespace sp

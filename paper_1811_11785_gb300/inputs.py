@@ -400,3 +400,91 @@ def random_mask(rng: np.random.Generator, T: int, B: int, keep: float) -> np.nda
     """A binary time-frequency mask ``[T][B]`` (uint8, 1 = keep) with each bin kept with
     probability ``keep``."""
     return (rng.random((T, B)) < keep).astype(np.uint8)
+
+
+# --------------------------------------------------------------------------------------
+# Synthetic shoebox rooms (the stand-in for Section 4's simulated rooms; TIMIT speech is not
+# available, so the source is white noise)
+# --------------------------------------------------------------------------------------
+
+def image_sources(src, room, beta, order):
+    """Image sources of a point source in a shoebox room [0, Lx] x [0, Ly] x [0, Lz] (the image
+    method of Allen and Berkley, 1979): for every axis, image index n and parity p give the
+    coordinate (1 - 2p) s + 2 n L, reflected |n - p| times on the wall at 0 and |n| times on the
+    wall at L.  beta = (b_x0, b_xL, b_y0, b_yL, b_z0, b_zL) are the walls' reflection
+    coefficients; images with more than `order` reflections in total are left out.  Returns
+    (positions [I][3], gains [I]) with the gains the product of the coefficients."""
+    src = np.asarray(src, dtype=np.float64)
+    pos, gain = [], []
+    rng_n = range(-order, order + 1)
+    for nx in rng_n:
+        for px in (0, 1):
+            rx0, rxL = abs(nx - px), abs(nx)
+            for ny in rng_n:
+                for py in (0, 1):
+                    ry0, ryL = abs(ny - py), abs(ny)
+                    for nz in rng_n:
+                        for pz in (0, 1):
+                            rz0, rzL = abs(nz - pz), abs(nz)
+                            if rx0 + rxL + ry0 + ryL + rz0 + rzL > order:
+                                continue
+                            pos.append([(1 - 2 * px) * src[0] + 2 * nx * room[0],
+                                        (1 - 2 * py) * src[1] + 2 * ny * room[1],
+                                        (1 - 2 * pz) * src[2] + 2 * nz * room[2]])
+                            gain.append(beta[0] ** rx0 * beta[1] ** rxL * beta[2] ** ry0 * beta[3] ** ryL *
+                                        beta[4] ** rz0 * beta[5] ** rzL)
+    return np.array(pos), np.array(gain)
+
+
+def room_impulse_responses(mic_pos, img_pos, img_gain, fs, c, length, half_width=16):
+    """RIRs [M][length]: every image contributes gain / (4 pi d) at the fractional delay
+    d fs / c samples, as a Hann-windowed sinc of 2 half_width + 1 taps."""
+    M = mic_pos.shape[0]
+    h = np.zeros((M, length))
+    taps = np.arange(-half_width, half_width + 1)
+    for m in range(M):
+        d = np.linalg.norm(img_pos - mic_pos[m][None, :], axis=1)
+        tau = d * fs / c
+        amp = img_gain / (4.0 * np.pi * d)
+        for t, a in zip(tau, amp):
+            n0 = int(np.floor(t))
+            idx = n0 + taps
+            ok = (idx >= 0) & (idx < length)
+            if not np.any(ok):
+                continue
+            x = idx - t
+            w = 0.5 + 0.5 * np.cos(np.pi * x / (half_width + 1))
+            h[m, idx[ok]] += a * (np.sinc(x) * w)[ok]
+    return h
+
+
+def room_signals(rng: np.random.Generator, mic_local: np.ndarray, S: int, fs: float, c: float,
+                 room=(10.0, 10.0, 3.0), beta_range=(0.2, 0.5), snr_range=(0.0, 30.0), order: int = 2,
+                 margin: float = 0.5):
+    """One room configuration: the array (mic_local around its centre) and a source placed
+    uniformly in the room at least `margin` from the walls and 1 m apart, wall reflection
+    coefficients uniform in beta_range, the image method to `order` reflections, a white
+    Gaussian source convolved with the RIRs, and independent white noise per channel at an SNR
+    uniform in snr_range (microphone-averaged).  Returns (samples [M][S] float32, s0 the unit
+    direction from the array centre to the source, beta, snr_db)."""
+    room = np.asarray(room, dtype=np.float64)
+    mic_local = np.asarray(mic_local, dtype=np.float64)
+    while True:
+        centre = margin + rng.random(3) * (room - 2 * margin)
+        src = margin + rng.random(3) * (room - 2 * margin)
+        if np.linalg.norm(src - centre) >= 1.0:
+            break
+    beta = rng.uniform(beta_range[0], beta_range[1], size=6)
+    snr = float(rng.uniform(*snr_range))
+    mics = centre[None, :] + mic_local
+    img, g = image_sources(src, room, beta, order)
+    dmax = np.max(np.linalg.norm(img - centre[None, :], axis=1)) + 0.2
+    length = int(np.ceil(dmax * fs / c)) + 40
+    h = room_impulse_responses(mics, img, g, fs, c, length)
+    s = rng.standard_normal(S + length)
+    nfft = 1 << int(np.ceil(np.log2(S + 2 * length)))
+    x = np.fft.irfft(np.fft.rfft(s, nfft)[None, :] * np.fft.rfft(h, nfft, axis=1), nfft, axis=1)[:, length:length + S]
+    p = np.mean(x ** 2)
+    x = x + rng.standard_normal(x.shape) * np.sqrt(p / 10.0 ** (snr / 10.0))
+    u = (src - centre) / np.linalg.norm(src - centre)
+    return x.astype(np.float32), u, beta, snr

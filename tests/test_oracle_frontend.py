@@ -117,3 +117,28 @@ def test_weighted_rmse_eq20():
     assert got == pytest.approx(np.sqrt(0.25 ** 2 + 0.75 ** 2 + 1.0), rel=1e-14)
     # the planar map folds the lower hemisphere: a mirrored estimate has no error
     assert F.rmse_weighted(np.array([[0.6, 0.0, -0.8]]), np.array([2.0]), np.array([0.6, 0.0, 0.8]), 2) == 0.0
+
+
+def test_image_sources_first_order_and_gains():
+    """The direct path and the six first-order images of a shoebox, with one coefficient each."""
+    room = (10.0, 8.0, 3.0)
+    beta = (0.1, 0.2, 0.3, 0.4, 0.5, 0.6)
+    pos, g = I.image_sources([1.0, 2.0, 1.5], room, beta, 1)
+    got = {tuple(np.round(p, 9)): gg for p, gg in zip(pos, g)}
+    want = {(1.0, 2.0, 1.5): 1.0, (-1.0, 2.0, 1.5): 0.1, (19.0, 2.0, 1.5): 0.2, (1.0, -2.0, 1.5): 0.3,
+            (1.0, 14.0, 1.5): 0.4, (1.0, 2.0, -1.5): 0.5, (1.0, 2.0, 4.5): 0.6}
+    assert set(got) == set(want)
+    for k, v in want.items():
+        assert got[k] == pytest.approx(v)
+    assert len(I.image_sources([1.0, 2.0, 1.5], room, beta, 2)[0]) == 25
+
+
+def test_rir_direct_path_delay_and_gain():
+    """Order 0: one windowed sinc at d fs / c with peak 1 / (4 pi d) for an integer delay."""
+    fs, c = 16000.0, 343.0
+    d = 343.0 * 100 / 16000.0                     # exactly 100 samples
+    mic = np.array([[d, 0.0, 0.0]])
+    h = I.room_impulse_responses(mic, np.zeros((1, 3)), np.ones(1), fs, c, 200)
+    assert np.argmax(np.abs(h[0])) == 100
+    assert h[0, 100] == pytest.approx(1.0 / (4 * np.pi * d), rel=1e-12)
+    assert np.all(np.abs(np.delete(h[0], 100)) < 1e-12)
