@@ -262,6 +262,19 @@ def kdtree_stats(sp, b, frames, torch, reps=3):
             "bytes_read_per_query": bytes_per_q}
 
 
+def bench_kdtree(sp, I, torch, T=32768):
+    """The k-d tree search alone on the 3-D 7-microphone array, Q = 10242 (level-5 grid), K = 71:
+    T frames of 1-2 white sources in isotropic noise (the array3d_q10242 workload), projected by
+    sp_project, then sp_kdtree_search with its visit statistics."""
+    wl = I.workload("array3d_q10242", T=T, seed_offset=11)
+    st = sp.build_steering(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"], wl["N"])
+    b = sp.svd_reduce(st, wl["delta"])
+    frames = torch.from_numpy(wl["frames"]).cuda()
+    out = kdtree_stats(sp, b, frames, torch)
+    out["workload"] = f"array3d_q10242: 7-mic 3-D array, Q=10242, N=512, K={b.K}, {T} frames"
+    return out
+
+
 C4_UNIQUE, C4_REPEAT = 32768, 32
 LEARNED_N_TOP, LEARNED_THETA = 8, 0.2
 
@@ -540,7 +553,7 @@ def main():
     ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16"])
     ap.add_argument("--frames", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the SRP / precision comparison lines")
-    ap.add_argument("--only", choices=["array3d", "batched", "c5", "samples", "sweep"], default=None,
+    ap.add_argument("--only", choices=["array3d", "batched", "c5", "samples", "sweep", "kdtree"], default=None,
                     help="run only one extra section and print its JSON (profiling runs)")
     ap.add_argument("--array3d-frames", type=int, default=C4_UNIQUE,
                     help="unique frames of the 3-D array section (repeated to 2^20 unless --only)")
@@ -572,6 +585,8 @@ def main():
             print(json.dumps(bench_samples(sp, I, torch)), flush=True)
         elif args.only == "sweep":
             print(json.dumps(bench_delta_sweep(sp, I, torch)), flush=True)
+        elif args.only == "kdtree":
+            print(json.dumps(bench_kdtree(sp, I, torch)), flush=True)
         else:
             print(json.dumps(bench_batched(sp, I, torch)), flush=True)
         return

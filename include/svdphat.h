@@ -43,6 +43,7 @@ extern "C" {
 #define SP_ECUDA    (-3)  /* a CUDA runtime/driver call failed                            */
 #define SP_ETIMEOUT (-4)  /* a bounded device wait gave up (see sp_check_status)          */
 #define SP_ENOTIMPL (-5)  /* combination of mode / precision / size not supported         */
+#define SP_EBOUNDS  (-6)  /* debug build only: a device bounds check failed (see sp_check_status) */
 
 typedef enum {
     SP_MODE_SRP = 0,             /* Eq. 9 + Eq. 6: argmax Re{W X} over all Q rows           */
@@ -336,7 +337,8 @@ int sp_weighted_doa_error(const sp_steering *st, const int32_t *idx_dev, const f
                           const double *s0, int alpha, double *rmse_out, void *stream);
 
 /* Synchronise stream and report a device-side failure recorded since the last call
- * (SP_ETIMEOUT if a bounded wait gave up), clearing it. */
+ * (SP_ETIMEOUT if a bounded wait gave up; SP_EBOUNDS if, in the SP_DEBUG build
+ * libsvdphat_debug.so, a device bounds check failed and its access was skipped), clearing it. */
 int sp_check_status(void *stream);
 
 /* Measurement aid (the paper has no counterpart): the FP32 fused multiply-add rate of the

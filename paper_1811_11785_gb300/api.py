@@ -102,10 +102,11 @@ def exported_symbols() -> list[str]:
 
 
 def lib():
-    """Load libsvdphat.so (built in-tree); raise if it is missing."""
+    """Load libsvdphat.so (built in-tree; SVDPHAT_LIB may name another build of it, e.g. the
+    SP_DEBUG build libsvdphat_debug.so); raise if it is missing."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = os.environ.get("SVDPHAT_LIB") or _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is not built; call paper_1811_11785_gb300.build.build() first")
         L = ctypes.CDLL(path)

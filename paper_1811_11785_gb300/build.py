@@ -38,21 +38,33 @@ def _deps() -> list[str]:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    return up_to_date_lib(LIB)
+
+
+LIB_DEBUG = os.path.join(BUILD, "libsvdphat_debug.so")
+
+
+def up_to_date_lib(lib: str) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    if up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra_flags: list[str] | None = None, debug: bool = False) -> str:
+    """Build libsvdphat.so, or with debug=True libsvdphat_debug.so: the same sources compiled with
+    -DSP_DEBUG (device bounds checks that record a failure in the status word and skip the
+    access; sp_check_status reports SP_EBOUNDS)."""
+    lib = LIB_DEBUG if debug else LIB
+    if up_to_date_lib(lib):
+        return lib
+    objdir = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    flags = NVCC_FLAGS + (["-DSP_DEBUG"] if debug else []) + (extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -65,13 +77,13 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

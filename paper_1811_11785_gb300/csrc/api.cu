@@ -477,6 +477,8 @@ int sp_localize_samples(const sp_basis *b, const float *samples_dev, long long n
 int sp_check_status(void *stream) {
     int status = 0;
     SP_TRY(read_and_clear_device_status((cudaStream_t)stream, &status));
+    if (status & 0x100)
+        return fail(SP_EBOUNDS, "a device bounds check of the debug build failed (status " + std::to_string(status) + ")");
     if (status != 0)
         return fail(SP_ETIMEOUT, "a bounded device wait gave up (status " + std::to_string(status) + ")");
     return SP_OK;

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.h"
+#include "debug.cuh"
 
 namespace sp {
 
@@ -133,7 +134,8 @@ constexpr int kNodeSmem = 96 * 1024;
 __global__ void __launch_bounds__(KD_WARPS * 32)
     kdtree_kernel(const float2 *__restrict__ Z, int T, int K, const KdNode *__restrict__ nodes_g, int n_nodes,
                   int nodes_in_smem, const float *__restrict__ leaf_pts, const int32_t *__restrict__ leaf_ids,
-                  int32_t *__restrict__ idx_out, float *__restrict__ proj_out, int32_t *__restrict__ visits) {
+                  int32_t *__restrict__ idx_out, float *__restrict__ proj_out, int32_t *__restrict__ visits,
+                  int n_buckets, int *status) {
     extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int dim = 2 * K;
@@ -191,9 +193,11 @@ __global__ void __launch_bounds__(KD_WARPS * 32)
             float bound = stk_bound[sp];
             __syncwarp();
             if (bound > best_d) continue;
+            if (!dcheck(node >= 0 && node < n_nodes, status)) continue;
             KdNode nd = nodes[node];
             ++n_nodes_seen;
             while (nd.dim >= 0) {
+                if (!dcheck(nd.dim < dim, status)) break;
                 const float diff = qv[nd.dim] - nd.split;
                 const int near_c = diff < 0.f ? node + 1 : nd.right;
                 const int far_c = diff < 0.f ? nd.right : node + 1;
@@ -206,19 +210,35 @@ __global__ void __launch_bounds__(KD_WARPS * 32)
                     ++sp;
                 }
                 node = near_c;
+                if (!dcheck(node >= 0 && node < n_nodes, status)) break;
                 nd = nodes[node];
                 ++n_nodes_seen;
             }
             __syncwarp();
+            if (nd.dim >= 0) continue;   // only after a failed debug check
             // leaf bucket: lane j scores point j
             ++n_leaves;
             const int bucket = nd.right;
+            if (!dcheck(bucket >= 0 && bucket < n_buckets, status)) continue;
             const float *pb = leaf_pts + (size_t)bucket * dim * 32 + lane;
-            float d2 = 0.f;
-            for (int d = 0; d < dim; ++d) {
-                const float df = qv[d] - pb[(size_t)d * 32];
-                d2 = fmaf(df, df, d2);
+            // four partial sums over interleaved dimensions, eight loads in flight per lane
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};
+            int d = 0;
+            for (; d + 8 <= dim; d += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldg(pb + (size_t)(d + u) * 32);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float df = qv[d + u] - v[u];
+                    s4[u & 3] = fmaf(df, df, s4[u & 3]);
+                }
             }
+            for (; d < dim; ++d) {
+                const float df = qv[d] - pb[(size_t)d * 32];
+                s4[0] = fmaf(df, df, s4[0]);
+            }
+            float d2 = (s4[0] + s4[1]) + (s4[2] + s4[3]);
             int id = leaf_ids[(size_t)bucket * 32 + lane];
             if (id < 0) {
                 d2 = __int_as_float(0x7f800000);
@@ -260,9 +280,11 @@ int launch_kdtree_stats(const sp_basis *b, const void *Z, int T, int32_t *idx, f
     if (smem > 48 * 1024) SP_TRY(ensure_max_smem((const void *)kdtree_kernel));
     const long long need = ((long long)T + KD_WARPS - 1) / KD_WARPS;
     const unsigned grid = (unsigned)std::min<long long>(need, 8LL * num_sms());
+    int *status = nullptr;
+    SP_TRY(device_status_ptr(&status));
     kdtree_kernel<<<grid, KD_WARPS * 32, smem, s>>>((const float2 *)Z, T, b->K, b->nodes.as<KdNode>(), b->n_nodes,
                                                      in_smem, b->leaf_pts.as<float>(), b->leaf_ids.as<int32_t>(),
-                                                     idx, proj, visits);
+                                                     idx, proj, visits, b->n_slots / 32, status);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -41,6 +41,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "debug.cuh"
 #include "ptx.cuh"
 
 namespace sp {
@@ -195,6 +196,11 @@ __global__ void __maxnreg__(128)
                 // first chunk at +8 in the second half, whose box starts one bin early)
                 const int u = f * kM + m, r = u >> 1;
                 const uint32_t mo = (u & 1) ? (uint32_t)(prm.e0_bytes + r * pitch1 + 8) : (uint32_t)(r * pitch0);
+                if (!dcheck((c % CPR) * 32 + mo + 32 <= (uint32_t)prm.slot_bytes, prm.status)) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) x[m][b] = make_float2(0.f, 0.f);
+                    continue;
+                }
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"

@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "common.h"
+#include "debug.cuh"
 #include "ptx.cuh"
 
 namespace sp {
@@ -33,7 +34,7 @@ constexpr long long kDrainCycles = 4000000000LL;
 
 struct Step4Params {
     const float2 *frames;
-    int T, M, B, n_pairs, n_slots;
+    int T, M, B, Q, n_pairs, n_slots;
     unsigned pair_bytes;   // 16 M B
     const float4 *tab;     // [Q][M]: d_m / N as float hi + lo, 64-bin step phasor (cos, sin)
     const int32_t *idx;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
         int n_valid = 0;
         int q = -1;
         if (t < prm.T) q = prm.idx[t];
+        if (q >= 0 && !dcheck(q < prm.Q, prm.status)) q = -1;
         if (q >= 0) {
             const float2 *fr = whole ? smem_frame : prm.frames + (size_t)t * M * B;
             // lane m: d_m / N (split into two floats) and the 64-bin step phasor, from the
@@ -201,6 +203,7 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
     p.T = T;
     p.M = st->M;
     p.B = st->B;
+    p.Q = st->Q;
     p.n_pairs = (T + 1) / 2;
     p.pair_bytes = pair_bytes;
     const unsigned slot_bytes = (pair_bytes + 127) / 128 * 128;

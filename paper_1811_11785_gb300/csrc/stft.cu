@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "common.h"
+#include "debug.cuh"
 
 namespace sp {
 namespace {
@@ -30,7 +31,7 @@ constexpr int kStftPoints = 2048;   // complex points per CTA (all its transform
 // exp(-2 pi i k / N) for k <= n.
 __global__ void __launch_bounds__(kStftThreads)
     stft_kernel(const float *__restrict__ x, long long ld, int M, int N, int lg_n, int hop, int T, int fpc,
-                const uint8_t *__restrict__ mask, float2 *__restrict__ out) {
+                const uint8_t *__restrict__ mask, float2 *__restrict__ out, int *status) {
     extern __shared__ float2 sbuf[];
     const int n = N / 2, B = n + 1, hn = n / 2;
     const int G = fpc * M;                       // transforms per group
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(kStftThreads)
             const float *row = x + (size_t)m * ld + (size_t)l * hop;
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
                 float2 v = make_float2(0.f, 0.f);
-                if (l < T) v = make_float2(win[2 * j] * row[2 * j], win[2 * j + 1] * row[2 * j + 1]);
+                if (l < T && dcheck((long long)l * hop + 2 * j + 1 < ld, status))
+                    v = make_float2(win[2 * j] * row[2 * j], win[2 * j + 1] * row[2 * j + 1]);
                 src[g * n + j] = v;
             }
         }
@@ -148,7 +150,9 @@ int launch_stft(const float *x, long long ld, int M, int N, int hop, int T, cons
     if (smem > 48 * 1024) SP_TRY(ensure_max_smem((const void *)stft_kernel));
     const long long groups = ((long long)T + fpc - 1) / fpc;
     const unsigned grid = (unsigned)std::min<long long>(groups, 8LL * num_sms());
-    stft_kernel<<<grid, kStftThreads, smem, s>>>(x, ld, M, N, lg_n, hop, T, fpc, mask, (float2 *)frames);
+    int *status = nullptr;
+    SP_TRY(device_status_ptr(&status));
+    stft_kernel<<<grid, kStftThreads, smem, s>>>(x, ld, M, N, lg_n, hop, T, fpc, mask, (float2 *)frames, status);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

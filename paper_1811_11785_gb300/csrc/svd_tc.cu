@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "common.h"
+#include "debug.cuh"
 #include "ptx.cuh"
 
 namespace sp {
@@ -909,7 +910,10 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             for (int base = 0; base < tmax; base += 2) {
                 const int c = base + c2;
                 int q = -1;
-                if (c < total) q = __ldg(prm.reps + (n <= kCap ? cand[r * kCap + c] : c));
+                if (c < total) {
+                    const int cls = n <= kCap ? cand[r * kCap + c] : c;
+                    if (dcheck(cls >= 0 && cls < prm.Qr, &g_status)) q = __ldg(prm.reps + cls);
+                }
                 float acc = 0.f;
                 if (q >= 0) {
                     const float2 *dq = prm.Dc32 + (size_t)q * K;

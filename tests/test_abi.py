@@ -152,3 +152,12 @@ def test_batch_and_proposal_calls_reject_bad_arguments(lib):
     assert lib.sp_proposal_dims(None, None, None, None, None, None) == api.SP_EINVAL
     assert lib.sp_proposal_train_step(None, None, None, None, 4, ctypes.c_float(1e-3), None, None) == api.SP_EINVAL
     lib.sp_proposal_destroy(None)
+
+
+def test_debug_build_compiles_and_exports_every_symbol():
+    """The SP_DEBUG build (device bounds checks) compiles for sm_103a and exports the same ABI."""
+    from paper_1811_11785_gb300 import build as B
+    path = B.build(debug=True)
+    L = ctypes.CDLL(path)
+    for name in header_functions():
+        assert hasattr(L, name), name
