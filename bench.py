@@ -5,7 +5,7 @@ B = 257 bins), Q = 2562 icosphere directions, K from delta = 1e-5 (K = 48), 65,5
 per step with one white-noise plane-wave source per frame at SNR U(-5, 20) dB (synthetic).
 A step is one pass of Algorithm 1's online path over the batch: PHAT -> Z = V^H X ->
 exhaustive Re{D Z} argmax (FP16 tensor cores, then FP32 rescoring of every class within the
-FP16 rounding bound of the best; frames with more than 16 such classes go to an FP32 scan
+FP16 rounding bound of the best; frames with more than 14 such classes go to an FP32 scan
 over every class on a device list, empty on this workload) -> Y_qbar from the row of W
 (online step 4): five kernel launches (GEMM1, scan, list scan, list finalize, step 4) and a
 4-byte reset of the list count.  The STFT batch (943 MB) is larger than L2, so no flush is
@@ -340,17 +340,32 @@ def bench_array3d(sp, I, torch, unique=C4_UNIQUE, repeat=C4_REPEAT):
     return out
 
 
-C5_UNIQUE, C5_REPEAT, C5_TRAIN = 8192, 8, 16384
+C5_FRAMES, C5_TRAIN, C5_CHUNK, C5_EPOCHS, C5_ORACLE = 65536, 1 << 21, 65536, 3, 256
+C5_N_TOP = (2, 4)    # cells of ~64 children: at most 512 candidates per frame (8 cells overflow it)
+
+
+def _oracle_srp_block(args):
+    """FP64 SRP-PHAT (Eq. 5, 9: Re{W X} with W from Eq. 4, 8 and X from Eq. 3, 7) of a frame
+    sample over a block of directions, W built 256 rows at a time.  Returns Y [frames][block]."""
+    import oracle as O
+    fr, tau, N = args
+    X = O.phat(fr)
+    out = np.empty((fr.shape[0], tau.shape[0]))
+    for q0 in range(0, tau.shape[0], 256):
+        out[:, q0:q0 + 256] = O.srp_scores(O.steering(tau[q0:q0 + 256], N), X)
+    return out
 
 
 def bench_c5(sp, I, torch):
     """The 16-mic array in a 5 cm-radius ball (the one of the ball16_n1024_q642 parity
     cases), N = 1024 (B = 513, P = 120, L = 61,560), on the level-6 grid (Q = 40,962): the
     exhaustive FP16 path and the learned proposal (level-3 cells, top-4 cells of ~64
-    children each) on 65,536 frames per pass (8,192 unique frames of 1-3 white sources in
-    white noise at -5..20 dB, repeated 8 times on the device).  No FP64 oracle exists at this
-    size (its basis needs the eigendecomposition of a 40,962 x 40,962 Gram), so agreement is
-    reported against the library's own FP32 exhaustive path on the unique frames."""
+    children each) on 65,536 reverberant frames per pass (1-3 white sources with exponential
+    tails, T60 0.2-0.6 s, white noise at -5..20 dB, drawn on the device).  The proposal trains
+    on 2^21 frames of the same generator (other seeds).  The FP64 oracle's SRP-PHAT (Eq. 5)
+    scores a 256-frame sample over all 40,962 directions on every host core (the section's
+    cpu_baseline); both searches are compared with its argmax on that sample."""
+    import oracle as O
     fs, c, N = 16000.0, 343.0, 1024
     mic = I.array_random_ball(np.random.default_rng([I.SEED_BASE + 7, 4]), 16)
     dirs = I.icosphere(6)
@@ -359,44 +374,87 @@ def bench_c5(sp, I, torch):
     b = sp.svd_reduce(st, 1e-5)
     torch.cuda.synchronize()
     basis_s = time.perf_counter() - t0
-    rng = np.random.default_rng(I.SEED_BASE + 60)
-    ev, _, _ = I.training_frames(rng, mic, C5_UNIQUE, N, fs, c)
-    uniq = torch.from_numpy(ev).cuda()
-    del ev
-    frames = uniq.repeat(C5_REPEAT, 1, 1)
+    frames, _, n_src = I.reverberant_frames_gpu(I.SEED_BASE + 60, mic, C5_FRAMES, N, fs, c)
     T = frames.shape[0]
-    tr, _, _ = I.training_frames(np.random.default_rng(I.SEED_BASE + 61), mic, C5_TRAIN, N, fs, c)
     p = sp.Proposal(b, I.icosphere(3), seed=5)
-    x, y = p.examples(torch.from_numpy(tr).cuda(), "fp16")
-    del tr
     t1 = time.perf_counter()
-    losses = p.train(x, y, epochs=6, batch=512, lr=1e-3, seed=6)
+    x = torch.empty((C5_TRAIN, p.F), dtype=torch.float32, device="cuda")
+    y = torch.empty(C5_TRAIN, dtype=torch.int32, device="cuda")
+    for i, r0 in enumerate(range(0, C5_TRAIN, C5_CHUNK)):
+        tr, _, _ = I.reverberant_frames_gpu(I.SEED_BASE + 1000 + i, mic, C5_CHUNK, N, fs, c)
+        x[r0:r0 + C5_CHUNK], y[r0:r0 + C5_CHUNK] = p.examples(tr, "fp16")
+        del tr
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    losses = p.train(x, y, epochs=C5_EPOCHS, batch=1024, lr=1e-3, seed=6)
+    torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     del x, y
 
-    ex16 = sp.localize(b, uniq, "svd_exhaustive", "fp16", score=False)[0]
-    ex32 = sp.localize(b, uniq, "svd_exhaustive", "fp32", score=False)[0]
-    li, _, _, fb = p.localize(uniq, "fp16", n_top=4, theta=LEARNED_THETA, score=False)
+    ex16, _, pr16 = sp.localize(b, frames, "svd_exhaustive", "fp16", score=False)
+    ex32 = sp.localize(b, frames, "svd_exhaustive", "fp32", score=False)[0]
+    res = {}
+    for nt in C5_N_TOP:
+        li, _, _, fb = p.localize(frames, "fp16", n_top=nt, theta=LEARNED_THETA, score=False)
+        res[nt] = (li, fb)
     torch.cuda.synchronize()
     ms = lambda fn, n: T / _rate(fn, n, T, torch) * 1000
     t_proj = ms(lambda: sp.project(b, frames, "fp16"), 3)
     t_exh = ms(lambda: sp.localize(b, frames, "svd_exhaustive", "fp16"), 3)
     t_exh_ns = ms(lambda: sp.localize(b, frames, "svd_exhaustive", "fp16", score=False), 3)
-    t_lrn = ms(lambda: p.localize(frames, "fp16", n_top=4, theta=LEARNED_THETA, fallback=False), 3)
+    t_lrn = {nt: ms(lambda: p.localize(frames, "fp16", n_top=nt, theta=LEARNED_THETA, fallback=False), 3)
+             for nt in C5_N_TOP}
+
+    # FP64 SRP-PHAT on a sample, every host core (the section's cpu_baseline)
+    rng = np.random.default_rng(I.SEED_BASE + 62)
+    sel = np.sort(rng.choice(T, C5_ORACLE, replace=False))
+    fr_s = frames[torch.from_numpy(sel).cuda()].cpu().numpy()
+    tau = O.tdoa_farfield(mic, dirs, fs, c)
+    pool = oracle_pool()
+    blocks = np.array_split(np.arange(tau.shape[0]), 2 * _cores())
+    t2 = time.perf_counter()
+    Y = np.concatenate(pool.map(_oracle_srp_block, [(fr_s, tau[bl], N) for bl in blocks]), axis=1)
+    oracle_s = time.perf_counter() - t2
+    ref, ymax = O.argmax_lowest(Y)
+    cls = O.direction_classes(tau)
+    L = st.L
+    unit = dirs / np.linalg.norm(dirs, axis=1, keepdims=True)
+
+    def vs_fp64(idx):
+        # on a 1-degree grid the runner-up is often a neighbour within 1e-4 L of the best, so
+        # besides the same-direction rate report the SRP-PHAT energy given up and the angle
+        i = idx.cpu().numpy()[sel]
+        same = cls[i] == cls[ref]
+        loss = (ymax - Y[np.arange(len(sel)), i]) / L
+        ang = np.degrees(np.arccos(np.clip(np.sum(unit[i] * unit[ref], axis=1), -1.0, 1.0)))
+        q = lambda v: {"median": float(np.median(v)), "p99": float(np.quantile(v, 0.99)), "max": float(v.max())}
+        return {"agreement": float(same.mean()), "energy_loss_over_L": q(loss), "angle_deg": q(ang)}
+
+    learned = {}
+    for nt in C5_N_TOP:
+        li, fb = res[nt]
+        learned[f"n_top_{nt}"] = {
+            "frames_per_s": T / t_lrn[nt] * 1000, "ms_per_pass": t_lrn[nt],
+            "fallback_fraction": float(fb.float().mean()),
+            "agreement_vs_exhaustive_fp16": float((li == ex16).float().mean()),
+            "vs_fp64_srp_phat": vs_fp64(li)}
     return {
         "workload": f"ball16_n1024_q40962: 16-mic array in a 5 cm-radius ball, N=1024, Q=40962, K={b.K}, "
-                    f"{T} frames per pass ({C5_UNIQUE} unique x {C5_REPEAT}), 1-3 white sources, white noise "
-                    f"-5..20 dB (no reverberation)",
+                    f"{T} frames per pass, 1-3 white sources with exponential reverberant tails "
+                    f"(T60 U(0.2, 0.6) s), white noise -5..20 dB",
         "svd_exhaustive_fp16_frames_per_s": T / t_exh * 1000,
-        "svd_learned_fp16_frames_per_s": T / t_lrn * 1000,
-        "ms_per_pass": {"gemm1": t_proj, "exhaustive_scan": t_exh_ns - t_proj,
-                        "step4": t_exh - t_exh_ns, "learned_total": t_lrn},
-        "gemm1_hbm_GBps": 8 * 16 * 513 * T / (t_proj * 1e-3) / 1e9,
+        "ms_per_pass": {"gemm1": t_proj, "exhaustive_scan": t_exh_ns - t_proj, "step4": t_exh - t_exh_ns},
+        "gemm1_tflops": 2.0 * T * 2 * L * 2 * b.K / (t_proj * 1e-3) / 1e12,
         "fp16_agreement_vs_fp32_path": float((ex16 == ex32).float().mean()),
-        "learned": {"n_top": 4, "theta": LEARNED_THETA, "cells": 642, "train_frames": C5_TRAIN, "epochs": 6,
-                    "train_s": train_s, "final_loss": float(losses[-1]),
-                    "fallback_fraction": float(fb.float().mean()),
-                    "agreement_vs_exhaustive_fp16": float((li == ex16).float().mean())},
+        "exhaustive_fp16_vs_fp64_srp_phat": vs_fp64(ex16),
+        "fp64_sample": {"frames": C5_ORACLE,
+                        "sources_per_frame": np.bincount(n_src.cpu().numpy()[sel], minlength=4)[1:].tolist()},
+        "learned": {"theta": LEARNED_THETA, "cells": p.C, "train_frames": C5_TRAIN, "epochs": C5_EPOCHS,
+                    "batch": 1024, "generate_and_label_s": gen_s, "train_s": train_s,
+                    "loss_per_epoch": [float(v) for v in losses], **learned},
+        "cpu_baseline": {"value": C5_ORACLE / oracle_s, "unit": "frames/s", "cores": _cores(), "kind": "oracle",
+                         "sample": f"FP64 SRP-PHAT (Eq. 5) of {C5_ORACLE} frames over all {tau.shape[0]} directions"},
         "basis_setup_s": basis_s,
     }
 

@@ -210,7 +210,7 @@ int sp_project(const sp_basis *b, const void *frames_dev, int T, sp_prec prec,
  *                              reduced-precision scan collects, per frame, every class
  *                              whose score lies within the scan's rounding bound of the
  *                              frame's maximum and rescores them in FP32 against FP32 Z
- *                              and D; a frame with more than 16 such classes is scored in
+ *                              and D; a frame with more than 14 such classes is scored in
  *                              FP32 against every class instead.  Either way the result
  *                              equals an FP32 scan of the same Z (up to FP32 summation
  *                              order).

@@ -183,10 +183,12 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
                     cudaStream_t s, int max_ctas = 0);
 // ws: scan_workspace_bytes(T) bytes, 256-byte aligned (list of the frames whose candidate
-// window overflows, their keys and a count).
+// window overflows, their keys and a count).  With rows/n_rows (device) only the frames
+// rows[0 .. *n_rows) of Z's T frames are scanned (and only their idx/proj written).
 size_t scan_workspace_bytes(int T);
 int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
-                    float *proj, cudaStream_t s, void *ws);
+                    float *proj, cudaStream_t s, void *ws, const int32_t *rows = nullptr,
+                    const int *n_rows = nullptr);
 int launch_kdtree(const sp_basis *b, const void *Z, int T, int32_t *idx, float *proj,
                   cudaStream_t s);
 int tc_prepare(sp_basis *b);

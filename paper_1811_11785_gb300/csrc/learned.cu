@@ -412,9 +412,8 @@ struct RescoreParams {
     int32_t *idx;
     float *proj;
     int32_t *fb_flag;    // [T] or null
-    int32_t *fb_list;    // frames that fall back
+    int32_t *fb_list;    // frames that fall back (to the exhaustive tensor-core scan)
     int *fb_count;
-    unsigned long long *keys;   // fallback result keys, zeroed here for the listed frames
 };
 
 __global__ void __launch_bounds__(256, 3) rescore_kernel(const RescoreParams prm) {
@@ -435,7 +434,6 @@ __global__ void __launch_bounds__(256, 3) rescore_kernel(const RescoreParams prm
     }
     if (!(cf >= prm.theta) || tp[0] < 0 || total == 0 || total > 32 * kMaxRounds) {
         if (lane == 0) {
-            prm.keys[frame] = 0ull;
             prm.fb_list[atomicAdd(prm.fb_count, 1)] = (int32_t)frame;
             if (prm.fb_flag) prm.fb_flag[frame] = 1;
         }
@@ -539,94 +537,6 @@ __global__ void to_half2_kernel(const float2 *in, int Q, int K, int Kp, __half2 
     const int q = (int)(i / Kp), k = (int)(i % Kp);
     const float2 v = k < K ? in[(size_t)q * K + k] : make_float2(0.f, 0.f);
     out[i] = __floats2half2_rn(v.x, v.y);
-}
-
-// The exhaustive Eq. 14 search for the frames that fell back, exact in FP32: a grid-stride
-// loop over items (8 frames, 256 direction classes); a thread scores one class for the 8
-// frames (Z in shared memory), the best per frame goes to a packed key by atomicMax
-// (score bits ordered, then the complement of the index so that ties keep the lowest).
-constexpr int kFbFrames = 8, kFbClasses = 256;
-
-struct FallbackParams {
-    const float2 *Z;
-    const int *count;
-    const int32_t *list;
-    int K, Qr;
-    const int32_t *reps;
-    const float2 *D;
-    unsigned long long *keys;   // per frame, zeroed by rescore_kernel for the listed frames
-};
-
-__device__ __forceinline__ unsigned long long pack_key(float v, int q) {
-    const uint32_t b = __float_as_uint(v);
-    const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-    return ((unsigned long long)o << 32) | (uint32_t)(0xFFFFFFFFu - (uint32_t)q);
-}
-
-__global__ void __launch_bounds__(256) fallback_scan_kernel(const FallbackParams prm) {
-    __shared__ float2 zs[kFbFrames][kMaxKp];
-    const int n = *prm.count, K = prm.K;
-    const int n_groups = (n + kFbFrames - 1) / kFbFrames, n_slices = (prm.Qr + kFbClasses - 1) / kFbClasses;
-    const int lane = threadIdx.x & 31;
-    for (int item = blockIdx.x; item < n_groups * n_slices; item += gridDim.x) {
-        const int g = item / n_slices, sl = item % n_slices;
-        __syncthreads();
-        for (int e = threadIdx.x; e < kFbFrames * K; e += blockDim.x) {
-            const int f = e / K, k = e % K, fi = g * kFbFrames + f;
-            zs[f][k] = fi < n ? prm.Z[(size_t)prm.list[fi] * K + k] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        const int r = sl * kFbClasses + threadIdx.x;
-        float acc[kFbFrames];
-#pragma unroll
-        for (int f = 0; f < kFbFrames; ++f) acc[f] = 0.f;
-        const int q = r < prm.Qr ? prm.reps[r] : -1;
-        if (q >= 0) {
-            const float2 *dq = prm.D + (size_t)q * K;
-            for (int k0 = 0; k0 < K; k0 += 8) {     // 8 loads in flight
-                float2 d[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) d[u] = k0 + u < K ? __ldg(dq + k0 + u) : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (k0 + u < K) {
-#pragma unroll
-                        for (int f = 0; f < kFbFrames; ++f) {
-                            acc[f] = fmaf(d[u].x, zs[f][k0 + u].x, acc[f]);
-                            acc[f] = fmaf(-d[u].y, zs[f][k0 + u].y, acc[f]);
-                        }
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int f = 0; f < kFbFrames; ++f) {
-            unsigned long long key = q >= 0 ? pack_key(acc[f], q) : 0ull;
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
-                key = ok > key ? ok : key;
-            }
-            const int fi = g * kFbFrames + f;
-            if (lane == 0 && fi < n && key) atomicMax(&prm.keys[prm.list[fi]], key);
-        }
-    }
-}
-
-__global__ void fallback_finalize_kernel(const int *count, const int32_t *list, const unsigned long long *keys,
-                                         int32_t *idx, float *proj) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= *count) return;
-    const int f = list[r];
-    const unsigned long long key = keys[f];
-    if (!key) {
-        idx[f] = -1;
-        if (proj) proj[f] = __int_as_float(0x7fc00000);
-        return;
-    }
-    idx[f] = (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
-    const uint32_t o = (uint32_t)(key >> 32);
-    if (proj) proj[f] = __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
 }
 
 // ---------------------------------------------------------------- training kernels
@@ -1204,15 +1114,16 @@ int sp_localize_learned(const sp_proposal *p, const void *frames_dev, int T, sp_
     const int K = b->K;
     const size_t zb = ((size_t)T * K * 8 + 255) / 256 * 256;
     const size_t nb = ((size_t)T * 4 + 255) / 256 * 256;
-    SP_TRY(p->lwork.reserve(zb + nb * (5 + kTop) + 256));
+    const size_t sb = (scan_workspace_bytes(T) + 255) / 256 * 256;
+    SP_TRY(p->lwork.reserve(zb + nb * (3 + kTop) + sb + 256));
     char *w = p->lwork.as<char>();
     float2 *Z = reinterpret_cast<float2 *>(w);
     float *zn2 = reinterpret_cast<float *>(w + zb);
     float *conf = reinterpret_cast<float *>(w + zb + nb);
     int32_t *fb_list = reinterpret_cast<int32_t *>(w + zb + 2 * nb);
     int32_t *top = reinterpret_cast<int32_t *>(w + zb + 3 * nb);
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(w + zb + (3 + kTop) * nb);   // 2 nb
-    int *fb_count = reinterpret_cast<int *>(w + zb + (5 + kTop) * nb);
+    void *scan_ws = w + zb + (3 + kTop) * nb;
+    int *fb_count = reinterpret_cast<int *>(w + zb + (3 + kTop) * nb + sb);
     SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, Z, zn2, s));
     SP_TRY(launch_mlp(p, Z, zn2, T, nullptr, top, conf, s));
     SP_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
@@ -1237,23 +1148,11 @@ int sp_localize_learned(const sp_proposal *p, const void *frames_dev, int T, sp_
     r.fb_flag = fallback_dev;
     r.fb_list = fb_list;
     r.fb_count = fb_count;
-    r.keys = keys;
     rescore_kernel<<<(unsigned)((T + 7) / 8), 256, 0, s>>>(r);
     SP_CUDA(cudaGetLastError());
-    FallbackParams f;
-    f.Z = Z;
-    f.count = fb_count;
-    f.list = fb_list;
-    f.K = K;
-    f.Qr = (int)b->st->reps.size();
-    f.reps = b->st->d_reps.as<int32_t>();
-    f.D = b->Dc32.as<float2>();
-    f.keys = keys;
-    fallback_scan_kernel<<<(unsigned)(2 * num_sms()), 256, 0, s>>>(f);
-    SP_CUDA(cudaGetLastError());
-    fallback_finalize_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(fb_count, fb_list, keys, idx_dev,
-                                                                          proj_score_dev);
-    SP_CUDA(cudaGetLastError());
+    // the frames that fell back: the exhaustive tensor-core scan of sp_localize on the listed
+    // frames only (CTAs past the device-side count exit at once)
+    SP_TRY(launch_svd_scan(b, Z, zn2, T, (int)prec, idx_dev, proj_score_dev, s, scan_ws, fb_list, fb_count));
     if (score_dev) SP_TRY(launch_score_row(b->st, frames_dev, T, idx_dev, score_dev, s));
     return SP_OK;
 }

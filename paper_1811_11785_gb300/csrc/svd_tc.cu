@@ -11,15 +11,15 @@
 //
 // svd_scan_kernel -- Eq. 13, Eq. 14 and the rescoring:
 //   Y = Re{D Z} = [Re D, -Im D] . [Re Z, Im Z] over tiles of 64 direction classes, FP16/BF16
-//   operands (Z rounded from FP32), FP32 in TMEM; Y never leaves the chip.  Pass 1 keeps each
-//   frame's maximum m.  Every scan score differs from its FP32 rescoring by at most
-//   e = 2.1 u sqrt(L) ||Z|| (u: unit roundoff of the operand type; sum_k |D_qk||Z_k| <=
-//   ||D_q|| ||Z|| and ||D_q|| <= ||W_q|| = sqrt(L)), so the FP32 winner scores at least
-//   m - 2e in the scan.  Pass 2 recomputes the scan and collects every class at or above
-//   m - 2e - 1e-6 L (at most 16 per frame; a frame with more is rescored against every
-//   class).  All collected classes are rescored in FP32 against FP32 Z and FP32 D; the best
-//   (ties -> lowest direction index) is the frame's direction.  The result equals an FP32
-//   scan of the same Z.
+//   operands (Z rounded from FP32), FP32 in TMEM; Y never leaves the chip.  Every scan score
+//   differs from its FP32 rescoring by at most e = 2.1 u sqrt(L) ||Z|| (u: unit roundoff of
+//   the operand type; sum_k |D_qk||Z_k| <= ||D_q|| ||Z|| and ||D_q|| <= ||W_q|| = sqrt(L)),
+//   so the FP32 winner scores at least m - 2e in the scan, m the frame's scan maximum.  One
+//   pass over the class tiles keeps a running maximum and every class at or above it minus
+//   2e + 2e-6 L (at most 14 per frame; a frame with more is rescored against every class);
+//   all kept classes are rescored in FP32 against FP32 Z and FP32 D, and the best (ties ->
+//   lowest direction index) is the frame's direction.  The result equals an FP32 scan of
+//   the same Z.  An optional device-side frame list restricts the scan to listed frames.
 //
 // K-dimension layout of GEMM1 (a permutation of the paper's column order p*B + k): the
 // contraction is cut into stages (bin chunk c of 4 bins, pair group g of <= 24 pairs);
@@ -92,7 +92,7 @@ constexpr int kEpiWarp0 = 16, kTmaWarp = 20, kMmaWarp = 21;
 constexpr int kZBuf = 256;            // TMEM column offset of the second Z buffer
 constexpr int kScanThreads = 256;     // 4 epilogue, 1 TMA, 1 MMA, 2 helper warps
 constexpr int kN2 = 64;               // direction classes per GEMM2 tile
-constexpr int kCap = 16;              // candidates kept per frame
+constexpr int kCap = 14;              // candidates kept per frame (two CTAs per SM at 2K <= 128)
 constexpr int kRingMax = 4;           // GEMM2 D-tile / TMEM buffers in flight (2 when 2K > 256)
 
 TcLayout make_tc_layout(int P, int B, int K) {
@@ -713,8 +713,10 @@ struct ScanParams {
     const float2 *Z;     // [T][K] complex64
     const float *zn2;    // [T] ||Z||^2
     int T, K, k2, k2_atoms, Qr, nq;
+    const int32_t *rows;   // optional frame list: tile position p scans frame rows[p], p < *n_rows
+    const int *n_rows;
     const int32_t *reps;
-    const float2 *Dc32;  // [Q][K] complex64
+    const float2 *Dr32;  // [Qr][K] complex64, the D rows of the class representatives
     float tol_z;         // 2 * 2.1 u sqrt(L): candidate window per unit ||Z||
     float tol_abs;       // 2 * 1e-6 L
     int *ovf_count;      // frames whose window holds more than kCap classes: count, list,
@@ -724,29 +726,41 @@ struct ScanParams {
     float *proj;
 };
 
+// One pass over the class tiles.  Per tile a frame's thread takes the tile maximum, raises
+// its running maximum m (dropping the kept classes that fall below the new m - window), then
+// keeps every class of the tile at or above m - window.  Since m only grows, the kept set at
+// the end is exactly {classes at or above m_final - window}.  Kept classes live in shared
+// memory as [slot][frame] (class, score), so the 128 threads touch 128 consecutive words.
 template <int BF16, int kRing>
 __global__ void __launch_bounds__(kScanThreads, 2)
     svd_scan_kernel(const __grid_constant__ CUtensorMap tmap_d, const ScanParams prm) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long t0 = (long long)blockIdx.x * 128;
+    const int T = prm.T;
+    // tile positions [0, n_pos) are live; a CTA past them has no work (uniform exit)
+    const int n_pos = prm.rows ? min(*prm.n_rows, T) : T;
+    if (t0 >= n_pos) return;
     const int k2_atoms = prm.k2_atoms;
     const int b2_bytes = k2_atoms * kN2 * 128;          // one D tile
     const int off_b2 = k2_atoms * kAtomBytes;
     const int off_cand = off_b2 + kRing * b2_bytes;
-    const int off_cnt = off_cand + 128 * kCap * 4;
-    const int off_bar = off_cnt + 128 * 4;
-    int *cand = reinterpret_cast<int *>(smem + off_cand);
+    const int off_cs = off_cand + 128 * kCap * 4;
+    const int off_cnt = off_cs + 128 * kCap * 4;
+    const int off_fr = off_cnt + 128 * 4;
+    const int off_bar = off_fr + 128 * 4;
+    int *cand = reinterpret_cast<int *>(smem + off_cand);       // [kCap][128] class
+    float *cand_s = reinterpret_cast<float *>(smem + off_cs);   // [kCap][128] scan score
     int *cnt_s = reinterpret_cast<int *>(smem + off_cnt);
+    int *fr_s = reinterpret_cast<int *>(smem + off_fr);         // frame of each row, -1 = none
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + off_bar);
     uint64_t *b2_full = bars + 0, *b2_empty = bars + kRing, *t2_full = bars + 2 * kRing, *t2_empty = bars + 3 * kRing;
     uint64_t *drain = bars + 4 * kRing;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4 * kRing + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 4 * kRing + 2);
     const long long budget = g_wait_budget;
-    const long long t0 = (long long)blockIdx.x * 128;
     const int K = prm.K;
-    const int T = prm.T;
 
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) {
@@ -758,6 +772,15 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
+    }
+    if (tid < 128) {
+        const long long pos = t0 + tid;
+        int f = -1;
+        if (pos < n_pos) {
+            f = prm.rows ? prm.rows[pos] : (int)pos;
+            if (!dcheck(f >= 0 && f < T, &g_status)) f = -1;
+        }
+        fr_s[tid] = f;
     }
     if (warp == 4 && lane == 0) ptx::prefetch_tmap(&tmap_d);
     if (warp == 5) {
@@ -776,7 +799,8 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * kScanThreads;
                 const int r = e / per_row, kk = e % per_row;
-                z[u] = (e < n_el && kk < K && t0 + r < T) ? prm.Z[(size_t)(t0 + r) * K + kk] : make_float2(0.f, 0.f);
+                const int f = e < n_el ? fr_s[r] : -1;
+                z[u] = (f >= 0 && kk < K) ? prm.Z[(size_t)f * K + kk] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -798,18 +822,17 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         *abort_flag = 1;
         atomicOr(&g_status, 1);
     };
-    const int n_jobs = 2 * prm.nq;  // pass 0 then pass 1 over the class tiles
+    const int n_jobs = prm.nq;
 
     if (warp < 4) {
         const int r = tid;  // TMEM lane = frame row
-        const long long frame = t0 + r;
-        const float win = prm.tol_z * sqrtf(frame < T ? prm.zn2[frame] : 0.f) + prm.tol_abs;
-        float m = -__int_as_float(0x7f800000), thr = 0.f;
+        const int frame = fr_s[r];
+        const float win = prm.tol_z * sqrtf(frame >= 0 ? prm.zn2[frame] : 0.f) + prm.tol_abs;
+        float m = -__int_as_float(0x7f800000), thr = m;
         int cnt = 0;
         for (int j = 0; j < n_jobs; ++j) {
             const int u = j % kRing;
-            const int tile = (j % prm.nq + (int)blockIdx.x) % prm.nq, pass = j / prm.nq;
-            if (j == prm.nq) thr = m - win;
+            const int tile = (j + (int)blockIdx.x) % prm.nq;
             if (ptx::warp_flag(abort_flag)) break;
             if (!ptx::mbar_wait_warp(&t2_full[u], (j / kRing) & 1, budget)) {
                 if (lane == 0) give_up();
@@ -820,24 +843,40 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 float v[kN2];
                 ptx::tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * kN2), v);
                 const int qb = tile * kN2;
-                if (pass == 0) {
+                const int lim = min(kN2, prm.Qr - qb);
+                float tm = -__int_as_float(0x7f800000);
 #pragma unroll
-                    for (int i = 0; i < kN2; ++i)
-                        if (qb + i < prm.Qr) m = fmaxf(m, v[i]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < kN2; ++i) {
-                        if (v[i] >= thr && qb + i < prm.Qr) {
-                            if (cnt < kCap) cand[r * kCap + cnt] = qb + i;
-                            ++cnt;
+                for (int i = 0; i < kN2; ++i)
+                    if (i < lim) tm = fmaxf(tm, v[i]);
+                if (tm > m) {   // new maximum: raise the window, drop what fell out of it
+                    m = tm;
+                    thr = m - win;
+                    int keep = 0;
+                    for (int c = 0; c < min(cnt, kCap); ++c) {
+                        const float sc = cand_s[c * 128 + r];
+                        if (sc >= thr) {
+                            cand_s[keep * 128 + r] = sc;
+                            cand[keep * 128 + r] = cand[c * 128 + r];
+                            ++keep;
                         }
+                    }
+                    cnt = cnt > kCap ? kCap + 1 : keep;   // an overflow stays one
+                }
+#pragma unroll
+                for (int i = 0; i < kN2; ++i) {
+                    if (i < lim && v[i] >= thr) {
+                        if (cnt < kCap) {
+                            cand[cnt * 128 + r] = qb + i;
+                            cand_s[cnt * 128 + r] = v[i];
+                        }
+                        cnt = min(cnt + 1, kCap + 1);
                     }
                 }
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(&t2_empty[u]);
         }
-        cnt_s[r] = (frame < T && m == m && thr == thr) ? cnt : 0;
+        cnt_s[r] = (frame >= 0 && m == m && thr == thr) ? cnt : 0;
     } else if (warp == 4) {
         if (lane == 0) {
             int issued = -1;
@@ -850,7 +889,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 }
                 ptx::mbar_arrive_expect_tx(&b2_full[u], (uint32_t)b2_bytes);
                 uint8_t *B2 = smem + off_b2 + u * b2_bytes;
-                const int tile = (j % prm.nq + (int)blockIdx.x) % prm.nq;  // CTAs start at different tiles
+                const int tile = (j + (int)blockIdx.x) % prm.nq;  // CTAs start at different tiles
                 for (int a = 0; a < k2_atoms; ++a)
                     ptx::tma_load_2d(B2 + a * kN2 * 128, &tmap_d, &b2_full[u], a * kAtomElems, tile * kN2);
                 issued = j;
@@ -893,30 +932,31 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     // -------- rescoring in FP32: a warp takes four frames at a time (8 lanes each); lane
     // (c, part) sums the terms k = part, part + 4, ... of candidate c, 2 candidates per round
     // (frames carry 1-2 candidates on typical inputs).  The terms of a 64-term block are
-    // loaded in one unrolled batch, so a round costs one L2 round trip after the class lookup.
+    // loaded in one unrolled batch from the class-indexed D copy, so a round costs one L2
+    // round trip; the class becomes a direction index once, at the end.
     if (!*abort_flag) {
         const int g4 = lane >> 3, c2 = (lane >> 2) & 1, part = lane & 3;
         for (int r0 = 4 * warp; r0 < 128; r0 += 4 * (kScanThreads / 32)) {
             const int r = r0 + g4;
-            const long long frame = t0 + r;
-            const bool live = frame < T;
+            const int frame = fr_s[r];
+            const bool live = frame >= 0;
             const int n = live ? cnt_s[r] : 0;
             const int total = n <= kCap ? n : 0;   // n > kCap: the FP32 list scan takes the frame
             const float2 *zr = prm.Z + (size_t)(live ? frame : 0) * K;
             float best = 0.f;
-            int bq = -1;
+            int bc = -1;
             int tmax = max(total, __shfl_xor_sync(0xffffffffu, total, 8));
             tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, 16));
             for (int base = 0; base < tmax; base += 2) {
                 const int c = base + c2;
-                int q = -1;
+                int cls = -1;
                 if (c < total) {
-                    const int cls = n <= kCap ? cand[r * kCap + c] : c;
-                    if (dcheck(cls >= 0 && cls < prm.Qr, &g_status)) q = __ldg(prm.reps + cls);
+                    const int v = cand[c * 128 + r];
+                    if (dcheck(v >= 0 && v < prm.Qr, &g_status)) cls = v;
                 }
                 float acc = 0.f;
-                if (q >= 0) {
-                    const float2 *dq = prm.Dc32 + (size_t)q * K;
+                if (cls >= 0) {
+                    const float2 *dq = prm.Dr32 + (size_t)cls * K;
                     for (int k0 = 0; k0 < K; k0 += 64) {
                         float2 d[16], z[16];
 #pragma unroll
@@ -936,19 +976,21 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 }
                 acc += __shfl_xor_sync(0xffffffffu, acc, 1);
                 acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                if (q >= 0 && (bq < 0 || acc > best || (acc == best && q < bq))) {
+                // classes are numbered in increasing order of their representative direction,
+                // so the lowest class of a tie is the lowest direction index
+                if (cls >= 0 && (bc < 0 || acc > best || (acc == best && cls < bc))) {
                     best = acc;
-                    bq = q;
+                    bc = cls;
                 }
             }
             // best over the 2 candidate groups of this 8-lane group
             {
                 const float ov = __shfl_xor_sync(0xffffffffu, best, 4);
-                const int oq = __shfl_xor_sync(0xffffffffu, bq, 4);
-                const bool take = (bq < 0) || (oq >= 0 && (ov > best || (ov == best && oq < bq)));
+                const int oc = __shfl_xor_sync(0xffffffffu, bc, 4);
+                const bool take = (bc < 0) || (oc >= 0 && (ov > best || (ov == best && oc < bc)));
                 if (take) {
                     best = ov;
-                    bq = oq;
+                    bc = oc;
                 }
             }
             if ((lane & 7) == 0 && live) {
@@ -957,8 +999,8 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                     prm.ovf_list[pos] = (int32_t)frame;
                     prm.ovf_keys[pos] = 0ull;
                 } else {
-                    prm.idx[frame] = bq;
-                    if (prm.proj) prm.proj[frame] = bq < 0 ? __int_as_float(0x7fc00000) : best;
+                    prm.idx[frame] = bc < 0 ? -1 : __ldg(prm.reps + bc);
+                    if (prm.proj) prm.proj[frame] = bc < 0 ? __int_as_float(0x7fc00000) : best;
                 }
             }
         }
@@ -1156,8 +1198,12 @@ static ProjKernel proj_kernel_for(const TcLayout &t, int bf, int M) {
 }
 
 // D tiles in flight of the scan: four, two when the Z tile and four D tiles would not fit (2K > 256)
+static int scan_smem_bytes(const TcLayout &t, int ring) {
+    return t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 2 * 128 * kCap * 4 + 2 * 128 * 4 +
+           (4 * ring + 3) * 8 + 1024;
+}
 static int scan_ring_for(const TcLayout &t) {
-    return 3 * t.k2_atoms * kAtomBytes + 128 * kCap * 4 <= 216 * 1024 ? kRingMax : 2;
+    return scan_smem_bytes(t, kRingMax) <= 232448 ? kRingMax : 2;
 }
 
 static ScanKernel scan_kernel_for(const TcLayout &t, int bf) {
@@ -1237,7 +1283,7 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
 size_t scan_workspace_bytes(int T) { return 256 + ((size_t)T * 4 + 255) / 256 * 256 + (size_t)T * 8; }
 
 int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, int prec, int32_t *idx,
-                    float *proj, cudaStream_t s, void *ws) {
+                    float *proj, cudaStream_t s, void *ws, const int32_t *rows, const int *n_rows) {
     if (T == 0) return SP_OK;
     SP_CHECK(ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, SP_EINVAL, "scan: workspace missing or misaligned");
     const TcLayout &t = b->tc;
@@ -1255,7 +1301,9 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     p.Qr = (int)b->st->reps.size();
     p.nq = (p.Qr + kN2 - 1) / kN2;
     p.reps = b->st->d_reps.as<int32_t>();
-    p.Dc32 = b->Dc32.as<float2>();
+    p.Dr32 = b->Dc32r.as<float2>();
+    p.rows = rows;
+    p.n_rows = n_rows;
     const double u = bf ? std::ldexp(1.0, -8) : std::ldexp(1.0, -11);  // unit roundoff
     const double L = (double)b->st->L;
     p.tol_z = (float)(2.0 * 2.1 * u * std::sqrt(L));
@@ -1268,8 +1316,7 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     p.ovf_keys = reinterpret_cast<unsigned long long *>(w + 256 + ((size_t)T * 4 + 255) / 256 * 256);
     SP_CUDA(cudaMemsetAsync(p.ovf_count, 0, sizeof(int), s));
     const int ring = scan_ring_for(t);
-    const int smem = t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 128 * kCap * 4 + 128 * 4 +
-                     (4 * ring + 3) * 8 + 1024;
+    const int smem = scan_smem_bytes(t, ring);
     SP_CHECK(smem <= 232448, SP_ENOTIMPL, "scan: shared-memory plan exceeds 227 KB");
     const ScanKernel kern = scan_kernel_for(t, bf);
     SP_TRY(ensure_max_smem((const void *)kern));

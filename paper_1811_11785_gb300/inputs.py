@@ -488,3 +488,79 @@ def room_signals(rng: np.random.Generator, mic_local: np.ndarray, S: int, fs: fl
     x = x + rng.standard_normal(x.shape) * np.sqrt(p / 10.0 ** (snr / 10.0))
     u = (src - centre) / np.linalg.norm(src - centre)
     return x.astype(np.float32), u, beta, snr
+
+
+# --------------------------------------------------------------------------------------
+# Reverberant frames generated on the device (the learned proposal's 2M-frame training sets)
+# --------------------------------------------------------------------------------------
+
+REVERB_DENSITY = 23.0      # reverberant energy per second at the onset, relative to the direct path
+REVERB_REFLECTIONS = 8     # reflections drawn per source and frame
+
+
+def reverberant_frames_gpu(seed: int, mic_xyz: np.ndarray, T: int, N: int, fs: float, c: float,
+                           max_sources: int = 3, snr_range=(-5.0, 20.0), t60_range=(0.2, 0.6),
+                           n_reflections: int = REVERB_REFLECTIONS, density: float = REVERB_DENSITY,
+                           device="cuda", chunk: int = 16384):
+    """STFT frames ``[T][M][N/2+1]`` (complex64 on ``device``) drawn with torch's seeded
+    generator: 1..max_sources white sources per frame from uniformly random directions, each
+    with an exponentially decaying reverberant tail, plus independent white noise per
+    microphone at SNR ~ U(snr_range) (mic-averaged, against the reverberant signal).
+
+    A source's spectrum is white complex Gaussian; microphone m receives a plane wave from u
+    advanced by fs/c r_m . u samples (a phase ramp over the bins).  Its tail is n_reflections
+    plane waves from uniformly random directions arriving t_r ~ U(0, T60) after the direct
+    path, T60 ~ U(t60_range); reflection r carries energy density * T60 / n_reflections *
+    10^(-6 t_r / T60) of the direct path's (a Monte Carlo sample of an energy envelope that
+    decays by 60 dB over T60, so the tail holds density * T60 / 13.8 of the direct energy:
+    -4.8 dB at T60 = 0.2 s, 0 dB at 0.6 s).  A reflection arriving a frame length or more
+    after the direct sound carries an earlier, uncorrelated stretch of a white source, so each
+    reflection gets its own white spectrum.  Returns (frames, directions [T][max_sources][3],
+    number of sources [T]); rows s >= n_sources of the directions are unused."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    mic = torch.as_tensor(np.asarray(mic_xyz, dtype=np.float64), device=device).float()
+    M, B = mic.shape[0], N // 2 + 1
+    kb = torch.arange(B, device=device, dtype=torch.float32)
+
+    def uniform(*shape):
+        return torch.rand(shape, generator=g, device=device, dtype=torch.float32)
+
+    def white(n):
+        re = torch.randn((n, 1, B), generator=g, device=device, dtype=torch.float32)
+        im = torch.randn((n, 1, B), generator=g, device=device, dtype=torch.float32)
+        return torch.complex(re, im) * np.float32(np.sqrt(0.5))
+
+    def unit(n):
+        v = torch.randn((n, 3), generator=g, device=device, dtype=torch.float32)
+        return v / v.norm(dim=1, keepdim=True)
+
+    def plane(u):   # (n, 3) -> (n, M, B): phase ramps of plane waves from u
+        d = (fs / c) * (u @ mic.T)
+        ph = (2.0 * np.pi / N) * d[:, :, None] * kb[None, None, :]
+        return torch.polar(torch.ones_like(ph), ph)
+
+    out = torch.empty((T, M, B), dtype=torch.complex64, device=device)
+    dirs = torch.zeros((T, max_sources, 3), dtype=torch.float32, device=device)
+    n_src = torch.randint(1, max_sources + 1, (T,), generator=g, device=device)
+    for t0 in range(0, T, chunk):
+        n = min(chunk, T - t0)
+        sig = torch.zeros((n, M, B), dtype=torch.complex64, device=device)
+        for s in range(max_sources):
+            active = (n_src[t0:t0 + n] > s).float()[:, None, None]
+            u = unit(n)
+            dirs[t0:t0 + n, s] = u
+            sig += active * white(n) * plane(u)
+            t60 = t60_range[0] + (t60_range[1] - t60_range[0]) * uniform(n, 1, 1)
+            for _ in range(n_reflections):
+                tr = uniform(n, 1, 1) * t60
+                amp = torch.sqrt(density * t60 / n_reflections * torch.pow(10.0, -6.0 * tr / t60))
+                sig += (active * amp) * white(n) * plane(unit(n))
+        ps = (sig.abs() ** 2).mean(dim=(1, 2))
+        snr = snr_range[0] + (snr_range[1] - snr_range[0]) * uniform(n)
+        re = torch.randn((n, M, B), generator=g, device=device, dtype=torch.float32)
+        im = torch.randn((n, M, B), generator=g, device=device, dtype=torch.float32)
+        scale = torch.sqrt(ps / (2.0 * torch.pow(10.0, snr / 10.0)))[:, None, None]
+        out[t0:t0 + n] = sig + torch.complex(re, im) * scale
+    return out, dirs.double(), n_src

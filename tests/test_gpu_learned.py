@@ -189,6 +189,16 @@ def test_learned_search_matches_oracle(theta_mode):
     assert np.max(np.abs(proj[ok] - obest[ok])) <= 2e-3 * L
     sref = O.score_row(d["tau"], idx, d["X"], d["wl"]["N"])     # Algorithm 1 online step 4
     assert np.max(np.abs(score.cpu().numpy() - sref)) <= 1e-5 * L
+    # frames that fell back ran sp_localize's exhaustive tensor-core scan on the same Z (the
+    # kept-class set of the one-pass scan does not depend on the tile order; only whether a
+    # frame's window overflowed on the way can, and then the FP32 list scan takes it)
+    fbm = fb.astype(bool)
+    if fbm.any():
+        ei, _, ep = sp.localize(b, d["frames"], "svd_exhaustive", "fp16")
+        ei, ep = ei.cpu().numpy()[fbm], ep.cpu().numpy()[fbm]
+        same = idx[fbm] == ei
+        assert same.mean() >= 0.99
+        assert np.max(np.abs(proj[fbm][same] - ep[same]), initial=0.0) <= 1e-5 * L
     if theta_mode == "always":
         assert fb.all()
         _agree(d, idx, Ysvd)
