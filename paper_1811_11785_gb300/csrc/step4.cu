@@ -30,6 +30,15 @@ constexpr int kTeams = 4;
 constexpr int kConsumerWarps = 4 * kTeams;
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
 constexpr float kZero2 = 1e-30f;
+constexpr float kTwoPi = 6.28318530717958648f;
+
+// -(k d / N) reduced to [-1/2, 1/2] cycles, with d / N = hi + lo (two floats): the product
+// k hi is split exactly (fmaf) so that the reduction loses nothing for k < 2^24
+__device__ __forceinline__ float cycles_frac(int k, float hi, float lo) {
+    const float kf = (float)k;
+    const float p0 = kf * hi;
+    return -((p0 - rintf(p0)) + fmaf(kf, lo, fmaf(kf, hi, -p0)));
+}
 constexpr long long kDrainCycles = 4000000000LL;
 
 struct Step4Params {
@@ -144,15 +153,35 @@ __global__ void __launch_bounds__(kThreads, 1) step4_bulk_kernel(const Step4Para
                 const float elo = __shfl_sync(0xffffffffu, my_lo, m);
                 stp[m] = make_float2(__shfl_sync(0xffffffffu, my_sc, m), __shfl_sync(0xffffffffu, my_ss, m));
                 if (m < M) {
-                    const float kf = (float)k_first;
-                    const float p0 = kf * ehi;
-                    const float r0 = (p0 - rintf(p0)) + fmaf(kf, elo, fmaf(kf, ehi, -p0));
                     float sn, cs;
-                    sincospif(-2.f * r0, &sn, &cs);
+                    __sincosf(kTwoPi * cycles_frac(k_first, ehi, elo), &sn, &cs);
                     ph[m] = make_float2(cs, sn);
                 }
             }
-            for (int k = k_first; k < B; k += 64) {
+            // the last bin (B - 1 = N/2 when 64 | N/2) lane-parallel: lane m < M takes microphone
+            // m, so the 64-bin loop below ends with a full warp
+            const int k_end = ((B - 1) & 63) == 0 ? B - 1 : B;
+            if (k_end < B && gh == 1) {
+                float sr = 0.f, si = 0.f;
+                if (lane < M) {
+                    const float2 x = fr[(size_t)lane * B + (B - 1)];
+                    const float mag2 = x.x * x.x + x.y * x.y;
+                    const bool valid = mag2 >= kZero2;
+                    const float r = valid ? rsqrtf(mag2) : 0.f;
+                    n_valid += valid ? 1 : 0;
+                    float sn, cs;
+                    __sincosf(kTwoPi * cycles_frac(B - 1, my_hi, my_lo), &sn, &cs);
+                    sr = (x.x * cs - x.y * sn) * r;   // x^ exp(i theta), theta = -2 pi (B-1) d / N
+                    si = (x.x * sn + x.y * cs) * r;
+                }
+#pragma unroll
+                for (int o = 1; o < MMAX; o <<= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (lane == 0) acc = fmaf(sr, sr, si * si);
+            }
+            for (int k = k_first; k < k_end; k += 64) {
                 float sr = 0.f, si = 0.f;
 #pragma unroll
                 for (int m = 0; m < MMAX; ++m) {

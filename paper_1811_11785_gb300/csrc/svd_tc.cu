@@ -90,9 +90,11 @@ constexpr int kProdWarps = 16;
 constexpr int kProjThreads = 22 * 32; // 16 producer, 4 epilogue, 1 TMA, 1 MMA warps
 constexpr int kEpiWarp0 = 16, kTmaWarp = 20, kMmaWarp = 21;
 constexpr int kZBuf = 256;            // TMEM column offset of the second Z buffer
-constexpr int kScanThreads = 256;     // 4 epilogue, 1 TMA, 1 MMA, 2 helper warps
+constexpr int kScanThreads = 320;     // 8 epilogue (2 per TMEM lane quadrant), 1 TMA, 1 MMA warps
+constexpr int kScanEpiWarps = 8, kScanTmaWarp = 8, kScanMmaWarp = 9;
 constexpr int kN2 = 64;               // direction classes per GEMM2 tile
 constexpr int kCap = 14;              // candidates kept per frame (two CTAs per SM at 2K <= 128)
+constexpr int kCapH = kCap / 2;       // per half tile (a frame's two epilogue threads)
 constexpr int kRingMax = 4;           // GEMM2 D-tile / TMEM buffers in flight (2 when 2K > 256)
 
 TcLayout make_tc_layout(int P, int B, int K) {
@@ -726,11 +728,31 @@ struct ScanParams {
     float *proj;
 };
 
-// One pass over the class tiles.  Per tile a frame's thread takes the tile maximum, raises
-// its running maximum m (dropping the kept classes that fall below the new m - window), then
-// keeps every class of the tile at or above m - window.  Since m only grows, the kept set at
-// the end is exactly {classes at or above m_final - window}.  Kept classes live in shared
-// memory as [slot][frame] (class, score), so the 128 threads touch 128 consecutive words.
+// One pass over the class tiles.  Each frame has two epilogue threads (warps w and w + 4 read
+// the same TMEM lanes), one per 32-class half of every tile.  Per tile a thread takes its
+// half's maximum (a tree, no branch per score), raises its running maximum m_h, and keeps every
+// class of its half at or above m_h - window with its exact score in a list of kCapH; when the
+// list is full the smallest of the list and the newcomer is let go and its score recorded.
+// After the pass m = max(m_0, m_1) and the kept classes at or above m - window are the window
+// exactly, unless a window class was let go -- which happens only when kCapH kept classes all
+// score higher, i.e. when the window holds more than kCapH classes of that half; the recorded
+// score tells (>= m - window), and such a frame goes to the FP32 list scan.  Neither the
+// decision nor the set depends on the tile order.  Kept classes live in shared memory as
+// [slot][frame] (class, score), so the 128 threads of a half touch 128 consecutive words.
+// v[i] for a run-time i without local memory: a 5-level select tree on the bits of i
+__device__ __forceinline__ float pick32(const float (&v)[32], int i) {
+    float a[16], b[8], c[4], d[2];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = (i & 16) ? v[k + 16] : v[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = (i & 8) ? a[k + 8] : a[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = (i & 4) ? b[k + 4] : b[k];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) d[k] = (i & 2) ? c[k + 2] : c[k];
+    return (i & 1) ? d[1] : d[0];
+}
+
 template <int BF16, int kRing>
 __global__ void __launch_bounds__(kScanThreads, 2)
     svd_scan_kernel(const __grid_constant__ CUtensorMap tmap_d, const ScanParams prm) {
@@ -747,13 +769,15 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     const int off_b2 = k2_atoms * kAtomBytes;
     const int off_cand = off_b2 + kRing * b2_bytes;
     const int off_cs = off_cand + 128 * kCap * 4;
-    const int off_cnt = off_cs + 128 * kCap * 4;
-    const int off_fr = off_cnt + 128 * 4;
+    const int off_fr = off_cs + 128 * kCap * 4;
     const int off_bar = off_fr + 128 * 4;
-    int *cand = reinterpret_cast<int *>(smem + off_cand);       // [kCap][128] class
-    float *cand_s = reinterpret_cast<float *>(smem + off_cs);   // [kCap][128] scan score
-    int *cnt_s = reinterpret_cast<int *>(smem + off_cnt);
+    int *cand = reinterpret_cast<int *>(smem + off_cand);       // [kCap][128] class (half h: slots h kCapH ..)
+    float *cand_s = reinterpret_cast<float *>(smem + off_cs);   // [kCap][128] score bound
     int *fr_s = reinterpret_cast<int *>(smem + off_fr);         // frame of each row, -1 = none
+    // after the pass the A operand is dead: the halves' counts and maxima go there
+    int *cnt_s = reinterpret_cast<int *>(smem);                  // [2][128]
+    float *mh_s = reinterpret_cast<float *>(smem + 1024);        // [2][128]
+    float *dr_s = reinterpret_cast<float *>(smem + 2048);        // [2][128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + off_bar);
     uint64_t *b2_full = bars + 0, *b2_empty = bars + kRing, *t2_full = bars + 2 * kRing, *t2_empty = bars + 3 * kRing;
     uint64_t *drain = bars + 4 * kRing;
@@ -767,7 +791,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             ptx::mbar_init(&b2_full[i], 1);
             ptx::mbar_init(&b2_empty[i], 1);
             ptx::mbar_init(&t2_full[i], 1);
-            ptx::mbar_init(&t2_empty[i], 128);
+            ptx::mbar_init(&t2_empty[i], 32 * kScanEpiWarps);
         }
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
@@ -782,8 +806,8 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         }
         fr_s[tid] = f;
     }
-    if (warp == 4 && lane == 0) ptx::prefetch_tmap(&tmap_d);
-    if (warp == 5) {
+    if (warp == kScanTmaWarp && lane == 0) ptx::prefetch_tmap(&tmap_d);
+    if (warp == kScanMmaWarp) {
         ptx::tmem_alloc(tmem_slot, kRing * kN2);
         ptx::tmem_relinquish();
     }
@@ -823,13 +847,20 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         atomicOr(&g_status, 1);
     };
     const int n_jobs = prm.nq;
+    int my_cnt = 0;
+    float my_m = 0.f, my_dropped = 0.f;
 
-    if (warp < 4) {
-        const int r = tid;  // TMEM lane = frame row
+    if (warp < kScanEpiWarps) {
+        const int hf = warp >> 2;               // which 32 classes of every tile
+        const int r = (warp & 3) * 32 + lane;   // TMEM lane = frame row
         const int frame = fr_s[r];
         const float win = prm.tol_z * sqrtf(frame >= 0 ? prm.zn2[frame] : 0.f) + prm.tol_abs;
+        const float kNaN = __int_as_float(0x7fc00000);
         float m = -__int_as_float(0x7f800000), thr = m;
+        float dropped = kNaN;   // the largest score let go (NaN: none; fmaxf skips it)
         int cnt = 0;
+        int *my_cand = cand + hf * kCapH * 128 + r;
+        float *my_cs = cand_s + hf * kCapH * 128 + r;
         for (int j = 0; j < n_jobs; ++j) {
             const int u = j % kRing;
             const int tile = (j + (int)blockIdx.x) % prm.nq;
@@ -839,45 +870,71 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 break;
             }
             ptx::tc_fence_after();
-            {
-                float v[kN2];
-                ptx::tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * kN2), v);
-                const int qb = tile * kN2;
-                const int lim = min(kN2, prm.Qr - qb);
-                float tm = -__int_as_float(0x7f800000);
+            float v[32];
+            ptx::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(u * kN2 + 32 * hf), v);
+            // the scores are in registers: hand the accumulator back to the MMA warp now
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&t2_empty[u]);
+            const int qb = tile * kN2 + 32 * hf;
+            const int lim = prm.Qr - qb;   // < 32 only in the last tile (NaN padding: never kept)
+            if (lim < 32) {
 #pragma unroll
-                for (int i = 0; i < kN2; ++i)
-                    if (i < lim) tm = fmaxf(tm, v[i]);
-                if (tm > m) {   // new maximum: raise the window, drop what fell out of it
-                    m = tm;
-                    thr = m - win;
-                    int keep = 0;
-                    for (int c = 0; c < min(cnt, kCap); ++c) {
-                        const float sc = cand_s[c * 128 + r];
-                        if (sc >= thr) {
-                            cand_s[keep * 128 + r] = sc;
-                            cand[keep * 128 + r] = cand[c * 128 + r];
-                            ++keep;
+                for (int i = 0; i < 32; ++i) v[i] = i < lim ? v[i] : kNaN;
+            }
+            // half-tile maximum by a tree (no branch per score)
+            float t[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) t[i] = fmaxf(v[i], v[i + 16]);
+#pragma unroll
+            for (int w = 8; w >= 1; w >>= 1) {
+#pragma unroll
+                for (int i = 0; i < w; ++i) t[i] = fmaxf(t[i], t[i + w]);
+            }
+            const float tm = t[0];
+            if (tm > m) {   // new maximum: raise the window (entries now below it go at the merge)
+                m = tm;
+                thr = m - win;
+            }
+            // classes at or above the window as a bit mask (no branch per score)
+            unsigned h = 0u;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (v[i] >= thr) h |= 1u << i;
+            // a lone hit is the half-tile maximum itself (tm >= it >= thr makes tm a hit too)
+            const bool lone = __popc(h) == 1;
+            while (h) {
+                const int i = __ffs(h) - 1;
+                h &= h - 1;
+                float x = tm;
+                if (!lone) x = pick32(v, i);
+                if (cnt < kCapH) {
+                    my_cand[cnt * 128] = qb + i;
+                    my_cs[cnt * 128] = x;
+                    ++cnt;
+                } else {   // full: the smaller of x and the list's minimum (stale entries first) goes
+                    int jm = 0;
+                    float sm = my_cs[0];
+                    for (int c = 1; c < kCapH; ++c) {
+                        const float sc = my_cs[c * 128];
+                        if (sc < sm) {
+                            sm = sc;
+                            jm = c;
                         }
                     }
-                    cnt = cnt > kCap ? kCap + 1 : keep;   // an overflow stays one
-                }
-#pragma unroll
-                for (int i = 0; i < kN2; ++i) {
-                    if (i < lim && v[i] >= thr) {
-                        if (cnt < kCap) {
-                            cand[cnt * 128 + r] = qb + i;
-                            cand_s[cnt * 128 + r] = v[i];
-                        }
-                        cnt = min(cnt + 1, kCap + 1);
+                    if (x > sm) {
+                        my_cand[jm * 128] = qb + i;
+                        my_cs[jm * 128] = x;
+                        dropped = fmaxf(dropped, sm);
+                    } else {
+                        dropped = fmaxf(dropped, x);
                     }
                 }
             }
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&t2_empty[u]);
         }
-        cnt_s[r] = (frame >= 0 && m == m && thr == thr) ? cnt : 0;
-    } else if (warp == 4) {
+        my_cnt = cnt;
+        my_m = m;
+        my_dropped = dropped;
+    } else if (warp == kScanTmaWarp) {
         if (lane == 0) {
             int issued = -1;
             for (int j = 0; j < n_jobs; ++j) {
@@ -898,7 +955,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
                 ptx::mbar_wait(&b2_full[j % kRing], (j / kRing) & 1, kDrainBudget);
         }
         __syncwarp();
-    } else if (warp == 5) {
+    } else if (warp == kScanMmaWarp) {
         if (lane == 0) {
             const uint32_t idesc = ptx::idesc_f16(128, kN2, BF16);
             const int steps = prm.k2 >> 4;
@@ -926,6 +983,36 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             ptx::mbar_wait(drain, 0, kDrainBudget);
         }
         __syncwarp();
+    }
+    __syncthreads();   // every MMA has completed: the A operand is dead
+    if (warp < kScanEpiWarps) {
+        const int hf = warp >> 2, r = (warp & 3) * 32 + lane;
+        cnt_s[hf * 128 + r] = my_cnt;
+        mh_s[hf * 128 + r] = my_m;
+        dr_s[hf * 128 + r] = my_dropped;
+    }
+    __syncthreads();
+    // merge a frame's two lists: m = max(m_0, m_1); the window is every class at or above
+    // m - window.  A half that had to let a class at or above it go (list full) sends the frame
+    // to the FP32 list scan; otherwise the entries at or above it are the window exactly (the
+    // decision and the set do not depend on the tile order).  The merged list goes to slots
+    // 0 .. n-1, its count to cnt_s[r].
+    if (tid < 128 && !*abort_flag) {
+        const int r = tid, frame = fr_s[r];
+        const int c0 = cnt_s[r], c1 = cnt_s[128 + r];
+        const float m = fmaxf(mh_s[r], mh_s[128 + r]);
+        const float thr = m - (prm.tol_z * sqrtf(frame >= 0 ? prm.zn2[frame] : 0.f) + prm.tol_abs);
+        int n = 0;
+        if (dr_s[r] >= thr || dr_s[128 + r] >= thr) {
+            n = kCap + 1;
+        } else {
+            for (int c = 0; c < c0 + c1; ++c) {
+                const int slot = c < c0 ? c : kCapH + (c - c0);
+                const float sc = cand_s[slot * 128 + r];
+                if (sc >= thr) cand[(n++) * 128 + r] = cand[slot * 128 + r];
+            }
+        }
+        cnt_s[r] = (frame >= 0 && m == m && thr == thr) ? n : 0;
     }
     __syncthreads();
 
@@ -1007,7 +1094,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == kScanMmaWarp) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, kRing * kN2);
     }
@@ -1199,7 +1286,7 @@ static ProjKernel proj_kernel_for(const TcLayout &t, int bf, int M) {
 
 // D tiles in flight of the scan: four, two when the Z tile and four D tiles would not fit (2K > 256)
 static int scan_smem_bytes(const TcLayout &t, int ring) {
-    return t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 2 * 128 * kCap * 4 + 2 * 128 * 4 +
+    return t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 2 * 128 * kCap * 4 + 128 * 4 +
            (4 * ring + 3) * 8 + 1024;
 }
 static int scan_ring_for(const TcLayout &t) {
