@@ -387,16 +387,16 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     }
 }
 
-// Re{D_q Z} over the children of the proposed cells, one warp per frame, one candidate per
-// lane (32 at a time).  Z sits in shared memory (read as broadcasts); lane c reads its
-// candidate's row of an FP16 copy of D (rows padded to 16-byte multiples) with 16-byte
-// loads, all in flight before use.  A screened score differs from the FP32 one by at most
+// Re{D_q Z} over the children of the proposed cells, one warp per frame.  Screening: the warp
+// takes four candidates at a time, eight lanes per candidate row of an FP16 copy of D (rows
+// padded to 16-byte multiples), so a load instruction touches four 128-byte lines instead of
+// 32; Z sits in shared memory.  A screened score differs from the FP32 one by at most
 // e = (2^-11 sqrt(L) + 2^-24 sqrt(K)) ||Z|| (relative FP16 rounding of D, with
 // sum_k |D_qk| |Z_k| <= ||D_q|| ||Z|| <= sqrt(L) ||Z||, plus the FP16 subnormal spacing), so
 // every candidate whose screened score is within 2e (+ FP32 slack) of the best is rescored
 // in FP32 and the best of those is the frame's direction: the result equals an FP32 search
-// over all the candidates.
-constexpr int kMaxRounds = 16;    // <= 512 candidates per frame
+// over all the candidates.  Screened scores and directions wait in shared memory.
+constexpr int kMaxCand = 512;     // candidates per frame
 constexpr int kMaxKp = 160;       // K <= 160
 
 struct RescoreParams {
@@ -416,8 +416,60 @@ struct RescoreParams {
     int *fb_count;
 };
 
+// FP16 screening of a frame's candidates (directions cq[0 .. total)): candidates c0 + 4h + g,
+// h < NR, on lanes 8g .. 8g + 7 (NR rows in flight per group); lane p of a group takes the
+// 16-byte pieces p, p + 8, ... (NU of them) of a row.  Scores go to sc[c]; returns the maximum.
+template <int NR, int NU>
+__device__ __forceinline__ float screen_fp16(const uint4 *__restrict__ Dh, int n16, int Kp, const int *cq, float *sc,
+                                             int total, const float2 *z, int lane) {
+    const int g = lane >> 3, pl = lane & 7;
+    float m = -__int_as_float(0x7f800000);
+    for (int c0 = 0; c0 < total; c0 += 4 * NR) {
+        int qq[NR];
+        uint4 v[NR][NU];
+#pragma unroll
+        for (int h = 0; h < NR; ++h) {
+            const int c = c0 + 4 * h + g;
+            qq[h] = c < total ? cq[c] : -1;
+            const uint4 *row = Dh + (size_t)(qq[h] >= 0 ? qq[h] : 0) * n16;
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+                v[h][u] = (qq[h] >= 0 && pl + 8 * u < n16) ? __ldg(row + pl + 8 * u) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int h = 0; h < NR; ++h) {
+            float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const uint32_t wv[4] = {v[h][u].x, v[h][u].y, v[h][u].z, v[h][u].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = (pl + 8 * u) * 4 + e;
+                    if (k < Kp) {
+                        const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&wv[e]));
+                        const float2 zz = z[k];
+                        acc0 = fmaf(d.x, zz.x, acc0);
+                        acc1 = fmaf(-d.y, zz.y, acc1);
+                    }
+                }
+            }
+            float s = acc0 + acc1;
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            if (qq[h] >= 0) {
+                m = fmaxf(m, s);
+                if (pl == 0) sc[c0 + 4 * h + g] = s;
+            }
+        }
+    }
+    return m;
+}
+
 __global__ void __launch_bounds__(256, 3) rescore_kernel(const RescoreParams prm) {
     __shared__ float2 zs[8][kMaxKp];
+    __shared__ float sc_s[8][kMaxCand];
+    __shared__ int cq_s[8][kMaxCand];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long frame = (long long)blockIdx.x * 8 + w;
     if (frame >= prm.T) return;   // whole warp
@@ -432,7 +484,7 @@ __global__ void __launch_bounds__(256, 3) rescore_kernel(const RescoreParams prm
         cnt[t] = cell >= 0 ? prm.cell_ptr[cell + 1] - lo[t] : 0;
         total += cnt[t];
     }
-    if (!(cf >= prm.theta) || tp[0] < 0 || total == 0 || total > 32 * kMaxRounds) {
+    if (!(cf >= prm.theta) || tp[0] < 0 || total == 0 || total > kMaxCand) {
         if (lane == 0) {
             prm.fb_list[atomicAdd(prm.fb_count, 1)] = (int32_t)frame;
             if (prm.fb_flag) prm.fb_flag[frame] = 1;
@@ -449,65 +501,36 @@ __global__ void __launch_bounds__(256, 3) rescore_kernel(const RescoreParams prm
     for (int o = 16; o >= 1; o >>= 1) zn2 += __shfl_xor_sync(0xffffffffu, zn2, o);
     __syncwarp();
     const float2 *z = zs[w];
-    // ---- screening in FP16, one candidate per lane and round
-    float sc[kMaxRounds];
-    int cq[kMaxRounds];
-    float m = -__int_as_float(0x7f800000);
-    const int rounds = (total + 31) / 32;
-    const int n16 = Kp / 4;   // 16-byte pieces per row
+    // ---- the candidate directions of the frame into shared memory (all loads in flight)
+    for (int c = lane; c < total; c += 32) {
+        int q = -1, pos = c;
 #pragma unroll
-    for (int rd = 0; rd < kMaxRounds; ++rd) {
-        sc[rd] = -__int_as_float(0x7f800000);
-        cq[rd] = -1;
-        if (rd < rounds) {
-            int q = -1, pos = rd * 32 + lane;
-#pragma unroll
-            for (int t = 0; t < kTop; ++t) {
-                if (q < 0 && pos < cnt[t]) q = prm.child[lo[t] + pos];
-                else if (q < 0) pos -= cnt[t];
-            }
-            if (q >= 0) {
-                const uint4 *row = prm.Dh + (size_t)q * n16;
-                float acc0 = 0.f, acc1 = 0.f;
-                for (int c0 = 0; c0 < n16; c0 += 8) {   // 8 loads in flight
-                    uint4 v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = c0 + u < n16 ? __ldg(row + c0 + u) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const uint32_t wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int k = (c0 + u) * 4 + e;
-                            if (k < Kp) {
-                                const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&wv[e]));
-                                const float2 zz = z[k];
-                                acc0 = fmaf(d.x, zz.x, acc0);
-                                acc1 = fmaf(-d.y, zz.y, acc1);
-                            }
-                        }
-                    }
-                }
-                sc[rd] = acc0 + acc1;
-                cq[rd] = q;
-                m = fmaxf(m, sc[rd]);
-            }
+        for (int t = 0; t < kTop; ++t) {
+            if (q < 0 && pos < cnt[t]) q = prm.child[lo[t] + pos];
+            else if (q < 0) pos -= cnt[t];
         }
+        cq_s[w][c] = q;
     }
+    __syncwarp();
+    // ---- screening in FP16
+    const int n16 = Kp / 4;   // 16-byte pieces per row (<= 40)
+    float m = n16 <= 24 ? screen_fp16<4, 3>(prm.Dh, n16, Kp, cq_s[w], sc_s[w], total, z, lane)
+                        : screen_fp16<2, 5>(prm.Dh, n16, Kp, cq_s[w], sc_s[w], total, z, lane);
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncwarp();
     const float thr = m - (prm.tol_z * sqrtf(zn2) + prm.tol_abs);
     // ---- FP32 rescoring of every candidate in the window, one at a time by the whole warp
     // (lanes over k, coalesced row reads); every lane ends with the same best
     float best = 0.f;
     int bq = -1;
-#pragma unroll
-    for (int rd = 0; rd < kMaxRounds; ++rd) {
-        unsigned sel = __ballot_sync(0xffffffffu, cq[rd] >= 0 && sc[rd] >= thr);
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        const int c = c0 + lane;
+        unsigned sel = __ballot_sync(0xffffffffu, c < total && cq_s[w][c] >= 0 && sc_s[w][c] >= thr);
         while (sel) {
             const int j = __ffs(sel) - 1;
             sel &= sel - 1;
-            const int q = __shfl_sync(0xffffffffu, cq[rd], j);
+            const int q = cq_s[w][c0 + j];
             const float2 *dq = prm.D + (size_t)q * K;
             float acc = 0.f;
             for (int k = lane; k < K; k += 32) {
