@@ -549,14 +549,21 @@ def bench_delta_sweep(sp, I, torch, n_cfg=12, seconds=1.0):
 N_STREAMS, N_CONFIGS = 256, 16
 
 
-def bench_batched(sp, I, torch):
-    """The batched form: 256 streams in one CUDA-graph launch (autotuned).  Stream s uses one
-    of 16 seeded configurations (array of 4-12 mics in a 5 cm-radius ball, Q in {642, 2562},
-    N in {256, 512}; bases built once per configuration) and its own 50-2000 frames (a
-    seeded slice of that configuration's 2000 frames).  Reported beside the same streams
-    localised one sp_localize call after another."""
-    cfgs = I.batched_streams(N_CONFIGS, M_range=(4, 12), Q_choices=(642, 2562), N_choices=(256, 512),
-                             T_range=(2000, 2000), seed_offset=100)
+def bench_batched(sp, I, torch, full=False):
+    """The batched form: 256 streams in one CUDA-graph launch (autotuned, the GEMM1 kernel choice
+    included).  Stream s uses one of 16 seeded configurations (array of 4-12 mics in a 5
+    cm-radius ball, Q in {642, 2562}, N in {256, 512}; with full=True the whole range: 4-16
+    mics, Q in {642, 2562, 10242}, N in {256, 512, 1024}; bases built once per configuration)
+    and its own 50-2000 frames (a seeded slice of that configuration's 2000 frames).  Reported
+    beside the same streams localised one sp_localize call after another, with the time to
+    autotune the plan and to build it again from the tune cache (a file in a temporary
+    directory)."""
+    if full:
+        cfgs = I.batched_streams(N_CONFIGS, M_range=(4, 16), Q_choices=(642, 2562, 10242),
+                                 N_choices=(256, 512, 1024), T_range=(2000, 2000), seed_offset=200)
+    else:
+        cfgs = I.batched_streams(N_CONFIGS, M_range=(4, 12), Q_choices=(642, 2562), N_choices=(256, 512),
+                                 T_range=(2000, 2000), seed_offset=100)
     bases, pools = [], []
     t0 = time.perf_counter()
     for wl in cfgs:
@@ -573,20 +580,37 @@ def bench_batched(sp, I, torch):
         sb.append(bases[c])
         sf.append(pools[c][o:o + T].contiguous())
     total = sum(f.shape[0] for f in sf)
-    t0 = time.perf_counter()
-    bt = sp.Batch(sb, sf, "svd_exhaustive", "fp16", autotune=True)
-    tune_s = time.perf_counter() - t0
+    with tempfile.TemporaryDirectory() as d:
+        sp.set_tune_cache(os.path.join(d, "tune.json"))
+        try:
+            t0 = time.perf_counter()
+            bt = sp.Batch(sb, sf, "svd_exhaustive", "fp16", autotune=True, tune_kernels=True)
+            torch.cuda.synchronize()
+            tune_s = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            bt2 = sp.Batch(sb, sf, "svd_exhaustive", "fp16", autotune=True, tune_kernels=True)
+            torch.cuda.synchronize()
+            cached_s = time.perf_counter() - t0
+            cached = bt2.info()["from_cache"]
+            del bt2
+        finally:
+            sp.set_tune_cache(None)
     g_rate = _rate(bt.run, 10, total, torch)
 
     def serial():   # FP32 where a basis has no tensor-core plan, as in the graph
         for b, f in zip(sb, sf):
-            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 320 else "fp16")
+            sp.localize(b, f, "svd_exhaustive", "fp32" if 2 * b.K > 288 else "fp16")
     s_rate = _rate(serial, 3, total, torch)
     ks = sorted({b.K for b in bases})
-    return {"workload": f"{N_STREAMS} streams, {total} frames, {N_CONFIGS} configurations (M 4-12, Q 642/2562, "
-                        f"N 256/512, K {ks[0]}-{ks[-1]}), 50-2000 frames per stream",
+    ms = sorted({b.steering.M for b in bases})
+    qs = sorted({b.steering.Q for b in bases})
+    ns = sorted({b.steering.N for b in bases})
+    return {"workload": f"{N_STREAMS} streams, {total} frames, {N_CONFIGS} configurations (M {ms[0]}-{ms[-1]}, "
+                        f"Q {'/'.join(map(str, qs))}, N {'/'.join(map(str, ns))}, K {ks[0]}-{ks[-1]}), "
+                        f"50-2000 frames per stream",
             "graph_frames_per_s": g_rate, "serial_frames_per_s": s_rate, "plan": bt.info(),
-            "basis_setup_s": setup_s, "autotune_s": tune_s}
+            "basis_setup_s": setup_s, "autotune_s": tune_s, "plan_from_cache_s": cached_s,
+            "plan_from_cache": cached}
 
 
 def _rate(fn, n, T, torch):
@@ -646,7 +670,7 @@ def main():
         elif args.only == "kdtree":
             print(json.dumps(bench_kdtree(sp, I, torch)), flush=True)
         else:
-            print(json.dumps(bench_batched(sp, I, torch)), flush=True)
+            print(json.dumps(bench_batched(sp, I, torch, full=True)), flush=True)
         return
 
     def lib_project(b, frames, prec, zout):

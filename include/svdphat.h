@@ -278,7 +278,7 @@ int sp_localize_host(const sp_basis *b, const void *frames_host, int T, sp_mode 
  * frames and all outputs.
  *
  * Arguments are checked as in sp_localize (SP_EINVAL for a NULL or misaligned pointer, T < 0
- * or T > 2^28), and a basis without a tensor-core plan (2K > 320) gives SP_ENOTIMPL.
+ * or T > 2^28), and a basis without a tensor-core plan (2K > 288) gives SP_ENOTIMPL.
  *
  * Warm-up: the first call on a device looks up the array's device address (with that
  * device current) and caches it, and the first launch of each kernel loads it and sets its
@@ -356,7 +356,7 @@ int sp_set_wait_budget(long long iterations);
  * of frames): n independent streams, each with its own basis (array, grid, N, K), frames
  * and frame count, localised by one CUDA-graph launch whose branches run concurrently.
  * Each stream computes exactly what sp_localize computes for it (same kernels, same
- * results); where a basis has no tensor-core path (2K > 320 or M > 16) an FP16/BF16 request
+ * results); where a basis has no tensor-core path (2K > 288 or M > 16) an FP16/BF16 request
  * runs that stream in FP32.
  *
  * sp_batch_create: bases[i] (must outlive the plan), frames_dev[i] (device [T[i]][M][B]
@@ -366,23 +366,50 @@ int sp_set_wait_budget(long long iterations);
  * plan's lifetime.  Synchronous: after the work already queued on `stream` (which may be
  * writing the frames), it runs every stream once (sizing the workspaces), then captures the
  * graph; with SP_BATCH_AUTOTUNE it builds and times the candidate launch
- * shapes (branches in {8, 32, 128, n} x tiles per GEMM1 CTA in {1, 2, 4}) and keeps the
- * fastest.  Errors: SP_EINVAL (bad arguments, per stream as sp_localize), SP_ECUDA.
+ * shapes (branches in {8, 32, 128, n} x tiles per GEMM1 CTA in {1, 2, 4}; with
+ * SP_BATCH_TUNE_KERNELS also x GEMM1 kernel: TMA-fed where it applies or register-fed,
+ * the latter tried only when some stream could use either) and keeps the fastest.  Without
+ * SP_BATCH_TUNE_KERNELS every stream's results are bit-identical to sp_localize's; with it,
+ * a 7-microphone stream may take the register-fed GEMM1, whose FP32 sums run in another
+ * order (its results then equal sp_localize's on a frame buffer 8 bytes off a 16-byte
+ * boundary, which takes that kernel).  With a tune cache set (sp_set_tune_cache), an
+ * autotuned plan first looks up the batch's signature (device, mode, precision, every
+ * stream's M, B, K, class count, T and precision) and, if present, takes that shape without
+ * measuring; otherwise it measures and stores the winner.  Errors: SP_EINVAL (bad
+ * arguments, per stream as sp_localize; a tune cache that exists but does not parse), SP_ECUDA.
  * sp_batch_run: one graph launch on stream (asynchronous).
- * sp_batch_info: the chosen shape, the measured milliseconds of one launch (autotuned
- * plans, else 0) and how many streams run in FP32.
+ * sp_batch_info: the chosen shape (proj_variant 0: TMA-fed GEMM1 where it applies, 1:
+ * register-fed), the measured milliseconds of one launch (autotuned plans, else 0), how many
+ * streams run in FP32, and whether the shape came from the tune cache.  Any out pointer may
+ * be NULL.
  * sp_localize_batched: create (no autotuning), run once, synchronise, destroy.
  * ================================================================================= */
 #define SP_BATCH_AUTOTUNE 1
+#define SP_BATCH_TUNE_KERNELS 2
 int sp_batch_create(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
                     sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
                     float *const *proj_dev, int flags, void *stream, sp_batch **out);
 int sp_batch_run(sp_batch *bt, void *stream);
-int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, float *ms, int *n_fp32);
+int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, int *proj_variant, float *ms,
+                  int *n_fp32, int *from_cache);
 void sp_batch_destroy(sp_batch *bt);
 int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
                         sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
                         float *const *proj_dev, void *stream);
+
+/* The autotune cache (host only; no device call): path of a JSON file holding
+ * {"format": "svdphat-tune-cache", "version": 1, "plans": {key: {"branches": b,
+ * "tiles_per_cta": t, "proj_variant": v, "ms": m}}}; NULL or "" disables it (the default).
+ * The file is created on the first store and rewritten whole through a temporary file and
+ * a rename; a file that exists but does not parse is never overwritten (SP_EINVAL).
+ * sp_tune_cache_get: *found = 1 and the stored shape if key is present, else *found = 0
+ * (out pointers other than found may be NULL).  sp_tune_cache_put: stores or replaces an
+ * entry (branches >= 1, tiles_per_cta in {1, 2, 4}, proj_variant in {0, 1}, ms >= 0).
+ * Keys: 1-512 printable ASCII characters without '"' or '\'.  Errors: SP_EINVAL. */
+int sp_set_tune_cache(const char *path);
+int sp_tune_cache_get(const char *key, int *branches, int *tiles_per_cta, int *proj_variant, float *ms,
+                      int *found);
+int sp_tune_cache_put(const char *key, int branches, int tiles_per_cta, int proj_variant, float ms);
 
 /* =================================================================================
  * Learned direction proposal (no counterpart in the paper).  The paper searches Eq. 14
@@ -405,9 +432,9 @@ int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *
 
 /* Create a proposal for basis b (which must outlive it): C cell directions cell_dirs
  * [C][3] (host, need not be unit length), hidden sizes H1, H2 (multiples of 64 in
- * [64, 256]), 1 <= C <= 4096, 2K <= 320.  Weights are drawn uniformly in
+ * [64, 256]), 1 <= C <= 4096, 2K <= 288 (the tensor-core plan of GEMM1).  Weights are drawn uniformly in
  * +-sqrt(6 / fan_in) from a counter-based generator keyed by seed; biases are 0.
- * Synchronous.  Errors: SP_EINVAL (bad arguments), SP_ENOTIMPL (2K > 320). */
+ * Synchronous.  Errors: SP_EINVAL (bad arguments), SP_ENOTIMPL (2K > 288). */
 int sp_proposal_create(const sp_basis *b, const double *cell_dirs, int C, int H1, int H2,
                        unsigned long long seed, sp_proposal **out);
 void sp_proposal_destroy(sp_proposal *p);

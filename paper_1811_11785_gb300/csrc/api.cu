@@ -310,7 +310,8 @@ namespace sp {
 // basis's own; a batch plan gives every stream its own so that streams run concurrently).
 // max_ctas > 0 caps the CTAs of the tensor-core GEMM1 kernel (tiles per CTA = tiles / cap).
 int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec, int32_t *idx_dev,
-                float *score_dev, float *proj_score_dev, cudaStream_t s, DevBuf &work, int max_ctas) {
+                float *score_dev, float *proj_score_dev, cudaStream_t s, DevBuf &work, int max_ctas,
+                int proj_variant) {
     const sp_steering *st = b->st;
     switch (mode) {
         case SP_MODE_SRP: {
@@ -334,7 +335,7 @@ int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
                 const size_t nbytes = ((size_t)T * 4 + 255) / 256 * 256;
                 SP_TRY(work.reserve(zbytes + nbytes + scan_workspace_bytes(T)));
                 float *zn2 = reinterpret_cast<float *>(work.as<char>() + zbytes);
-                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, zn2, s, max_ctas));
+                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, zn2, s, max_ctas, proj_variant));
                 SP_TRY(launch_svd_scan(b, work.p, zn2, T, (int)prec, idx_dev, proj_score_dev, s,
                                        work.as<char>() + zbytes + nbytes));
             }
@@ -352,7 +353,7 @@ int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, 
             } else {
                 SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL, "bad precision");
                 SP_TRY(work.reserve(zbytes));
-                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, nullptr, s, max_ctas));
+                SP_TRY(launch_svd_proj(b, frames_dev, T, (int)prec, work.p, nullptr, s, max_ctas, proj_variant));
                 SP_TRY(launch_kdtree(b, work.p, T, idx_dev, proj_score_dev, s));
             }
             break;

@@ -9,11 +9,17 @@
 //
 // Autotuner: candidate launch shapes are (number of graph branches the streams are spread
 // over) x (tiles per CTA of the GEMM1 kernel: 1, 2 or 4, i.e. a CTA cap of tiles / d per
-// stream); each candidate graph is built and timed (one warm-up, three timed launches with
-// CUDA events) and the fastest is kept.
+// stream) x (with SP_BATCH_TUNE_KERNELS, the GEMM1 kernel: the TMA-fed one where it applies,
+// or the register-fed one -- tried only when some stream could use either; the two sum Z's
+// terms in different orders); each candidate graph is built and timed
+// (one warm-up, three timed launches with CUDA events) and the fastest is kept.  With a tune
+// cache set (sp_set_tune_cache) the chosen shape is stored under the batch's signature
+// (device, mode, precision, every stream's M, B, K, classes, T and precision) and a later plan
+// with the same signature takes it from the file without measuring.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <memory>
 #include <new>
 #include <string>
@@ -37,8 +43,9 @@ struct sp_batch {
     cudaEvent_t fork = nullptr;
     cudaStream_t origin = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int branches = 0, tiles_per_cta = 1;
+    int branches = 0, tiles_per_cta = 1, proj_variant = 0;
     float ms = 0.f;                     // measured time of one launch (autotuned plans)
+    int from_cache = 0;                 // the shape came from the tune cache
     ~sp_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         for (auto s : side) cudaStreamDestroy(s);
@@ -51,15 +58,47 @@ struct sp_batch {
 namespace sp {
 namespace {
 
-int enqueue_stream(sp_batch *bt, int i, cudaStream_t s, int tiles_per_cta) {
+int enqueue_stream(sp_batch *bt, int i, cudaStream_t s, int tiles_per_cta, int proj_variant) {
     const int tiles = (bt->T[i] + 127) / 128;
     const int cap = std::max(1, (tiles + tiles_per_cta - 1) / tiles_per_cta);
     return localize_ws(bt->b[i], bt->frames[i], bt->T[i], bt->mode, bt->prec[i], bt->idx[i], bt->score[i],
-                       bt->proj[i], s, *bt->work[i], cap);
+                       bt->proj[i], s, *bt->work[i], cap, proj_variant);
+}
+
+// The batch's signature: device, mode, precision, and a 64-bit FNV-1a hash of every stream's
+// (M, B, K, classes, T, precision, TMA-fed GEMM1 applicable).
+int plan_key(const sp_batch *bt, std::string *key) {
+    int dev = 0, sms = 0, maj = 0, mnr = 0;
+    SP_CUDA(cudaGetDevice(&dev));
+    SP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SP_CUDA(cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev));
+    SP_CUDA(cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev));
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&h](long long v) {
+        for (int k = 0; k < 8; ++k) {
+            h ^= (uint64_t)((v >> (8 * k)) & 0xff);
+            h *= 1099511628211ULL;
+        }
+    };
+    for (int i = 0; i < bt->n; ++i) {
+        const sp_steering *st = bt->b[i]->st;
+        mix(st->M);
+        mix(st->B);
+        mix(bt->b[i]->K);
+        mix((long long)st->reps.size());
+        mix(bt->T[i]);
+        mix((int)bt->prec[i]);
+        mix(proj_tma_applies(bt->b[i], bt->frames[i]) ? 1 : 0);
+    }
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "sm%d%d-%dsm/mode%d/prec%d/n%d/%016llx", maj, mnr, sms, (int)bt->mode,
+                  bt->n > 0 ? (int)bt->prec[0] : 0, bt->n, (unsigned long long)h);
+    *key = buf;
+    return SP_OK;
 }
 
 // Capture every stream's kernels into one graph: stream i on branch i % branches.
-int build_graph(sp_batch *bt, int branches, int tiles_per_cta, cudaGraphExec_t *out) {
+int build_graph(sp_batch *bt, int branches, int tiles_per_cta, int proj_variant, cudaGraphExec_t *out) {
     *out = nullptr;
     while ((int)bt->side.size() < branches) {
         cudaStream_t s;
@@ -75,7 +114,8 @@ int build_graph(sp_batch *bt, int branches, int tiles_per_cta, cudaGraphExec_t *
     if (cudaEventRecord(bt->fork, bt->origin) != cudaSuccess) rc = fail(SP_ECUDA, "batch: fork record");
     for (int k = 0; k < branches && rc == SP_OK; ++k)
         if (cudaStreamWaitEvent(bt->side[k], bt->fork, 0) != cudaSuccess) rc = fail(SP_ECUDA, "batch: fork wait");
-    for (int i = 0; i < bt->n && rc == SP_OK; ++i) rc = enqueue_stream(bt, i, bt->side[i % branches], tiles_per_cta);
+    for (int i = 0; i < bt->n && rc == SP_OK; ++i)
+        rc = enqueue_stream(bt, i, bt->side[i % branches], tiles_per_cta, proj_variant);
     for (int k = 0; k < branches && rc == SP_OK; ++k) {
         if (cudaEventRecord(bt->join[k], bt->side[k]) != cudaSuccess ||
             cudaStreamWaitEvent(bt->origin, bt->join[k], 0) != cudaSuccess)
@@ -129,7 +169,7 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
     *out = nullptr;
     SP_CHECK(n >= 1 && n <= 65536, SP_EINVAL, "sp_batch_create: n must be in [1, 65536]");
     SP_CHECK(bases && frames_dev && T && idx_dev, SP_EINVAL, "sp_batch_create: null array");
-    SP_CHECK((flags & ~SP_BATCH_AUTOTUNE) == 0, SP_EINVAL, "sp_batch_create: bad flags");
+    SP_CHECK((flags & ~(SP_BATCH_AUTOTUNE | SP_BATCH_TUNE_KERNELS)) == 0, SP_EINVAL, "sp_batch_create: bad flags");
     SP_CHECK(prec == SP_PREC_FP32 || prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL,
              "sp_batch_create: bad precision");
     for (int i = 0; i < n; ++i) {
@@ -161,39 +201,67 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
     SP_CUDA(cudaStreamWaitEvent(bt->origin, bt->fork, 0));
     // one eager pass: sizes every workspace (no allocation happens while capturing) and
     // sets the kernels' attributes
-    for (int i = 0; i < n; ++i) SP_TRY(enqueue_stream(bt.get(), i, bt->origin, 1));
+    for (int i = 0; i < n; ++i) SP_TRY(enqueue_stream(bt.get(), i, bt->origin, 1, 0));
     SP_CUDA(cudaStreamSynchronize(bt->origin));
     std::vector<int> br_cand;
     for (int k : {8, 32, 128})
         if (k < n) br_cand.push_back(k);
     br_cand.push_back(n);
     if (flags & SP_BATCH_AUTOTUNE) {
-        float best = 0.f;
-        for (int br : br_cand)
-            for (int tpc : {1, 2, 4}) {
-                cudaGraphExec_t ex = nullptr;
-                SP_TRY(build_graph(bt.get(), br, tpc, &ex));
-                float ms = 0.f;
-                const int rc = time_graph(ex, bt->origin, &ms);
-                if (rc != SP_OK) {
-                    cudaGraphExecDestroy(ex);
-                    return rc;
-                }
-                if (!bt->exec || ms < best) {
-                    if (bt->exec) cudaGraphExecDestroy(bt->exec);
-                    bt->exec = ex;
-                    best = ms;
-                    bt->branches = br;
-                    bt->tiles_per_cta = tpc;
-                } else {
-                    cudaGraphExecDestroy(ex);
-                }
-            }
-        bt->ms = best;
+        std::string key;
+        TunedShape cached{0, 0, 0, 0.f};
+        bool found = false;
+        if (tune_cache_enabled()) {
+            SP_TRY(plan_key(bt.get(), &key));
+            key += (flags & SP_BATCH_TUNE_KERNELS) ? "/k" : "";
+            if (tune_cache_get(key, &cached, &found) != SP_OK) found = false;   // unreadable file: tune
+            if (found && !(cached.branches >= 1 && cached.branches <= n &&
+                           (cached.tiles_per_cta == 1 || cached.tiles_per_cta == 2 || cached.tiles_per_cta == 4) &&
+                           (cached.proj_variant == 0 || cached.proj_variant == 1)))
+                found = false;
+        }
+        if (found) {
+            SP_TRY(build_graph(bt.get(), cached.branches, cached.tiles_per_cta, cached.proj_variant, &bt->exec));
+            bt->branches = cached.branches;
+            bt->tiles_per_cta = cached.tiles_per_cta;
+            bt->proj_variant = cached.proj_variant;
+            bt->ms = cached.ms;
+            bt->from_cache = 1;
+        } else {
+            bool both = false;   // kernel choice asked for, and some stream could run either GEMM1 kernel
+            for (int i = 0; i < n && (flags & SP_BATCH_TUNE_KERNELS); ++i)
+                both = both || (bt->prec[i] != SP_PREC_FP32 && proj_tma_applies(bases[i], frames_dev[i]));
+            float best = 0.f;
+            for (int pv = 0; pv < (both ? 2 : 1); ++pv)
+                for (int br : br_cand)
+                    for (int tpc : {1, 2, 4}) {
+                        cudaGraphExec_t ex = nullptr;
+                        SP_TRY(build_graph(bt.get(), br, tpc, pv, &ex));
+                        float ms = 0.f;
+                        const int rc = time_graph(ex, bt->origin, &ms);
+                        if (rc != SP_OK) {
+                            cudaGraphExecDestroy(ex);
+                            return rc;
+                        }
+                        if (!bt->exec || ms < best) {
+                            if (bt->exec) cudaGraphExecDestroy(bt->exec);
+                            bt->exec = ex;
+                            best = ms;
+                            bt->branches = br;
+                            bt->tiles_per_cta = tpc;
+                            bt->proj_variant = pv;
+                        } else {
+                            cudaGraphExecDestroy(ex);
+                        }
+                    }
+            bt->ms = best;
+            if (!key.empty())
+                SP_TRY(tune_cache_put(key, TunedShape{bt->branches, bt->tiles_per_cta, bt->proj_variant, best}));
+        }
     } else {
         bt->branches = std::min(n, 32);
         bt->tiles_per_cta = 1;
-        SP_TRY(build_graph(bt.get(), bt->branches, 1, &bt->exec));
+        SP_TRY(build_graph(bt.get(), bt->branches, 1, 0, &bt->exec));
     }
     *out = bt.release();
     return SP_OK;
@@ -205,10 +273,13 @@ int sp_batch_run(sp_batch *bt, void *stream) {
     return SP_OK;
 }
 
-int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, float *ms, int *n_fp32) {
+int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, int *proj_variant, float *ms, int *n_fp32,
+                  int *from_cache) {
     SP_CHECK(bt, SP_EINVAL, "sp_batch_info: null plan");
     if (branches) *branches = bt->branches;
     if (tiles_per_cta) *tiles_per_cta = bt->tiles_per_cta;
+    if (proj_variant) *proj_variant = bt->proj_variant;
+    if (from_cache) *from_cache = bt->from_cache;
     if (ms) *ms = bt->ms;
     if (n_fp32) {
         int c = 0;

@@ -180,8 +180,10 @@ int launch_step4_bulk(const sp_steering *st, const void *frames, int T, const in
                       cudaStream_t s);   // SP_ENOTIMPL where its plan does not apply
 // tensor-core path: Z = V^H X (PHAT fused) into z_out [T][K] complex64, then the Re{D Z} scan
 // (zn2_out [T] receives ||Z||^2 per frame, may be null; the scan needs it)
+// proj_variant: 0 = the TMA-fed kernel where its plan applies (7 microphones), else the
+// register-fed one; 1 = always the register-fed kernel
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
-                    cudaStream_t s, int max_ctas = 0);
+                    cudaStream_t s, int max_ctas = 0, int proj_variant = 0);
 // ws: scan_workspace_bytes(T) bytes, 256-byte aligned (list of the frames whose candidate
 // window overflows, their keys and a count).  With rows/n_rows (device) only the frames
 // rows[0 .. *n_rows) of Z's T frames are scanned (and only their idx/proj written).
@@ -222,7 +224,18 @@ int reduce_basis(const sp_steering *st, double delta, sp_basis *b);
 int install_basis(sp_basis *b);   // device copies of b->V, b->D (host FP64, filled)
 int build_kdtree(sp_basis *b);
 int localize_ws(const sp_basis *b, const void *frames_dev, int T, sp_mode mode, sp_prec prec, int32_t *idx_dev,
-                float *score_dev, float *proj_score_dev, cudaStream_t s, DevBuf &work, int max_ctas);
+                float *score_dev, float *proj_score_dev, cudaStream_t s, DevBuf &work, int max_ctas,
+                int proj_variant = 0);
+// whether the TMA-fed GEMM1 applies to this basis and frame buffer
+bool proj_tma_applies(const sp_basis *b, const void *frames);
+// autotune cache of batch plans (tunecache.cu): the file set by sp_set_tune_cache
+struct TunedShape {
+    int branches, tiles_per_cta, proj_variant;
+    float ms;
+};
+bool tune_cache_enabled();
+int tune_cache_get(const std::string &key, TunedShape *out, bool *found);
+int tune_cache_put(const std::string &key, const TunedShape &v);
 int check_localize_args(const sp_basis *b, const void *frames_dev, int T, const int32_t *idx_dev,
                         const float *score_dev, const float *proj_score_dev);
 int build_classes(sp_steering *st);   // rep_of / reps from the TDOA table (host)

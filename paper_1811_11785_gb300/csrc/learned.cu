@@ -905,7 +905,8 @@ int sp_proposal_create(const sp_basis *b, const double *cell_dirs, int C, int H1
     SP_CHECK(C >= 1 && C <= kMaxC, SP_EINVAL, "sp_proposal_create: C must be in [1, 4096]");
     SP_CHECK(H1 >= 64 && H1 <= kMaxH && H1 % 64 == 0 && H2 >= 64 && H2 <= kMaxH && H2 % 64 == 0, SP_EINVAL,
              "sp_proposal_create: hidden sizes must be multiples of 64 in [64, 256]");
-    SP_CHECK(2 * b->K <= kMaxF && b->K <= kMaxKp, SP_ENOTIMPL, "sp_proposal_create: 2K must be <= 320");
+    SP_CHECK(2 * b->K <= kMaxF && b->K <= kMaxKp && b->tc.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
+             "sp_proposal_create: the basis needs the tensor-core plan of GEMM1 (2K <= 288, M <= 16)");
     for (int c = 0; c < C; ++c) {
         const double *d = cell_dirs + 3 * c;
         SP_CHECK(std::isfinite(d[0]) && std::isfinite(d[1]) && std::isfinite(d[2]) &&

@@ -51,7 +51,7 @@ extern "C" int sp_localize_noalloc(const sp_basis *b, const void *frames_dev, in
     SP_CHECK(prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_ENOTIMPL,
              "sp_localize_noalloc: only SP_PREC_FP16 and SP_PREC_BF16");
     SP_CHECK(b->tc.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "sp_localize_noalloc: the tensor-core path supports 2K <= 320 and M <= 16");
+             "sp_localize_noalloc: the tensor-core path supports 2K <= 288 and M <= 16");
     const size_t zbytes = ((size_t)T * b->K * 8 + 255) / 256 * 256;
     const size_t nbytes = ((size_t)T * 4 + 255) / 256 * 256;
     const size_t need = zbytes + nbytes + scan_workspace_bytes(T);

@@ -392,6 +392,12 @@ __global__ void __maxnreg__(128)
 
 }  // namespace
 
+bool proj_tma_applies(const sp_basis *b, const void *frames) {
+    const TcLayout &t = b->tc;
+    return b->st->M == kM && (b->st->B & 1) == 1 && (reinterpret_cast<uintptr_t>(frames) & 15) == 0 && t.n1 > 0 &&
+           t.n1 <= 224 && tc_vmap_binmajor(b, 0) != nullptr;
+}
+
 int launch_svd_proj_tma(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
                         cudaStream_t s, int max_ctas) {
     if (T == 0) return SP_OK;

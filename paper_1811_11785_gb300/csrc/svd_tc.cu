@@ -84,7 +84,8 @@ constexpr int kGroupPairs = 24;       // pairs per stage group (3 atoms)
 constexpr int kAtomElems = 64;        // 16-bit elements per swizzle atom row
 constexpr int kAtomBytes = 128 * 128; // one 128-row atom
 constexpr int kGroupElems = 3 * kAtomElems;
-constexpr int kMaxN1 = 320;           // GEMM1 N limit (two MMAs of N <= 256 above 256)
+constexpr int kMaxN1 = 288;           // GEMM1 N limit: two MMAs of N <= 256 above 256, and two V
+                                      // stages of 3 atoms x n1 rows (2 x 3 x 128 n1 B) in 216 KB
 constexpr int kMaxN1Smem = 144;       // widest basis of the shared-memory A plan
 constexpr int kProdWarps = 16;
 constexpr int kProjThreads = 22 * 32; // 16 producer, 4 epilogue, 1 TMA, 1 MMA warps
@@ -1313,11 +1314,11 @@ int prepare_tc(const sp_basis *b, int prec) {
 }
 
 int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void *z_out, float *zn2_out,
-                    cudaStream_t s, int max_ctas) {
+                    cudaStream_t s, int max_ctas, int proj_variant) {
     if (T == 0) return SP_OK;
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "tensor-core path supports 2K <= 320 and M <= 16 (use SP_PREC_FP32)");
+             "tensor-core path supports 2K <= 288 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
     ProjParams p;
@@ -1335,7 +1336,7 @@ int launch_svd_proj(const sp_basis *b, const void *frames, int T, int prec, void
     p.zn2_out = zn2_out;
     p.n_tiles = (int)(((long long)T + 127) / 128);
     const int grid = std::min(p.n_tiles, max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms());
-    {   // the TMA-fed kernel for 7-microphone arrays where its plan applies
+    if (proj_variant == 0) {   // the TMA-fed kernel for 7-microphone arrays where its plan applies
         const int rc = launch_svd_proj_tma(b, frames, T, prec, z_out, zn2_out, s, max_ctas);
         if (rc != SP_ENOTIMPL) return rc;
     }
@@ -1375,7 +1376,7 @@ int launch_svd_scan(const sp_basis *b, const void *Z, const float *zn2, int T, i
     SP_CHECK(ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, SP_EINVAL, "scan: workspace missing or misaligned");
     const TcLayout &t = b->tc;
     SP_CHECK(t.n1 > 0 && b->tc_maps, SP_ENOTIMPL,
-             "tensor-core path supports 2K <= 320 and M <= 16 (use SP_PREC_FP32)");
+             "tensor-core path supports 2K <= 288 and M <= 16 (use SP_PREC_FP32)");
     const int bf = prec == SP_PREC_BF16 ? 1 : 0;
     const TcMaps *maps = reinterpret_cast<const TcMaps *>(b->tc_maps);
     ScanParams p;

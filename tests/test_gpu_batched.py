@@ -16,7 +16,7 @@ _S = {}
 
 def _wide_stream(T=300):
     """A stream whose basis is too wide for the tensor-core plan: 8 mics in a 15 cm-radius ball,
-    N = 512, Q = 642 gives K = 181 (2K = 362 > 320), so the batch runs it in FP32."""
+    N = 512, Q = 642 gives K = 181 (2K = 362 > 288), so the batch runs it in FP32."""
     rng = np.random.default_rng([I.SEED_BASE + 9, 8])
     mic = I.array_random_ball(rng, 8, radius=0.15)
     src = I.random_directions(rng, T)[:, None, :]
@@ -56,7 +56,7 @@ def test_batch_equals_per_stream_localize(prec, autotune):
     if autotune:
         assert info["ms"] > 0
     for i, (b, f) in enumerate(zip(bases, frames)):
-        ref_prec = "fp32" if 2 * b.K > 320 or b.steering.M > 16 else prec   # no tensor-core plan
+        ref_prec = "fp32" if 2 * b.K > 288 or b.steering.M > 16 else prec   # no tensor-core plan
         idx, score, proj = sp.localize(b, f, "svd_exhaustive", ref_prec)
         assert torch.equal(bt.idx[i], idx), i
         assert torch.equal(bt.proj[i], proj), i
@@ -67,7 +67,7 @@ def test_localize_batched_matches_and_agrees_with_oracle():
     wls, bases, frames = _streams()
     idx, score, proj = sp.localize_batched(bases, frames, "svd_exhaustive", "fp16")
     for i in range(len(bases)):
-        ref_prec = "fp32" if 2 * bases[i].K > 320 else "fp16"
+        ref_prec = "fp32" if 2 * bases[i].K > 288 else "fp16"
         ref = sp.localize(bases[i], frames[i], "svd_exhaustive", ref_prec)
         assert torch.equal(idx[i], ref[0]) and torch.equal(proj[i], ref[2])
     # every stream of at most 8 microphones (the wide FP32 one included) against the FP64 oracle:
@@ -75,7 +75,7 @@ def test_localize_batched_matches_and_agrees_with_oracle():
     # agreement over the pooled frames of these streams
     same_all = []
     checked = [i for i, wl in enumerate(wls) if wl["mic_xyz"].shape[0] <= 8]
-    assert any(2 * bases[i].K > 320 for i in checked)
+    assert any(2 * bases[i].K > 288 for i in checked)
     for i in checked:
         wl = wls[i]
         tau = O.tdoa_farfield(wl["mic_xyz"], wl["dirs"], wl["fs"], wl["c"])
@@ -94,11 +94,11 @@ def test_localize_batched_matches_and_agrees_with_oracle():
 
 
 def test_batch_mixes_tensor_core_and_fp32_streams():
-    """A basis beyond the tensor-core plan (2K > 320) runs its stream in FP32 inside the same
+    """A basis beyond the tensor-core plan (2K > 288) runs its stream in FP32 inside the same
     launch, with the same result as sp_localize in FP32."""
     wls, bases, frames = _streams()
-    big = [i for i, b in enumerate(bases) if 2 * b.K > 320]
-    small = [i for i, b in enumerate(bases) if 2 * b.K <= 320]
+    big = [i for i, b in enumerate(bases) if 2 * b.K > 288]
+    small = [i for i, b in enumerate(bases) if 2 * b.K <= 288]
     assert big and small, "the streams must mix wide (FP32) and tensor-core bases"
     sel = big[:2] + small[:2]
     bt = sp.Batch([bases[i] for i in sel], [frames[i] for i in sel], "svd_exhaustive", "fp16")
@@ -114,7 +114,7 @@ def test_batch_mixes_tensor_core_and_fp32_streams():
 @pytest.mark.parametrize("mode,prec", [("svd_kdtree", "fp16"), ("svd_exhaustive", "bf16")])
 def test_batch_other_modes_equal_per_stream(mode, prec):
     wls, bases, frames = _streams()
-    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 320][:6]
+    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 288][:6]
     bt = sp.Batch([bases[i] for i in sel], [frames[i] for i in sel], mode, prec)
     bt.run()
     torch.cuda.synchronize()
@@ -128,7 +128,7 @@ def test_localize_batched_waits_for_the_callers_stream():
     """Frames written by work still queued on the caller's stream (behind a long device-side
     delay) are what the batch localises: the plan's set-up and run are ordered after it."""
     wls, bases, frames = _streams()
-    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 320][:3]
+    sel = [i for i, b in enumerate(bases) if 2 * b.K <= 288][:3]
     refs = [sp.localize(bases[i], frames[i], "svd_exhaustive", "fp16")[0] for i in sel]
     bufs = [torch.zeros_like(frames[i]) for i in sel]
     torch.cuda.synchronize()
@@ -141,3 +141,57 @@ def test_localize_batched_waits_for_the_callers_stream():
     torch.cuda.synchronize()
     for a, r in zip(idx, refs):
         assert torch.equal(a, r)
+
+
+def _offset_copy(f):
+    """A copy of f whose data starts 8 bytes off a 16-byte boundary (the register-fed GEMM1)."""
+    flat = torch.empty(f.numel() + 1, dtype=f.dtype, device=f.device)
+    v = flat[1:].view(f.shape)
+    v.copy_(f)
+    return v
+
+
+def test_autotuned_plan_is_stored_and_reused(tmp_path):
+    """An autotuned plan with a tune cache stores its shape under the batch's signature; a
+    second plan for the same batch takes it from the file (no measurement) and gives the same
+    results; another batch has another signature.  With the kernel choice tuned, a stream on
+    the register-fed GEMM1 equals sp_localize on a buffer that takes that kernel."""
+    import json
+    wls, bases, frames = _streams()
+    path = tmp_path / "tune.json"
+    sp.set_tune_cache(path)
+    try:
+        b1 = sp.Batch(bases, frames, "svd_exhaustive", "fp16", autotune=True, tune_kernels=True)
+        i1 = b1.info()
+        assert not i1["from_cache"] and i1["ms"] > 0
+        plans = json.loads(path.read_text())["plans"]
+        assert len(plans) == 1
+        (key, entry), = plans.items()
+        assert key.endswith("/k")
+        assert entry["branches"] == i1["branches"] and entry["tiles_per_cta"] == i1["tiles_per_cta"]
+        assert entry["proj_variant"] == i1["proj_variant"]
+        b2 = sp.Batch(bases, frames, "svd_exhaustive", "fp16", autotune=True, tune_kernels=True)
+        i2 = b2.info()
+        assert i2["from_cache"]
+        assert all(i2[k] == i1[k] for k in ("branches", "tiles_per_cta", "proj_variant"))
+        b1.run()
+        b2.run()
+        torch.cuda.synchronize()
+        sp.check_status()
+        for i in range(len(bases)):
+            assert torch.equal(b1.idx[i], b2.idx[i]) and torch.equal(b1.proj[i], b2.proj[i]), i
+            b, f = bases[i], frames[i]
+            if 2 * b.K > 288:
+                continue
+            ref = f
+            if i1["proj_variant"] == 1 and b.steering.M == 7:
+                ref = _offset_copy(f)
+            idx, score, proj = sp.localize(b, ref, "svd_exhaustive", "fp16")
+            assert torch.equal(b1.idx[i], idx) and torch.equal(b1.proj[i], proj), i
+        b3 = sp.Batch(bases[:-1], frames[:-1], "svd_exhaustive", "fp16", autotune=True, tune_kernels=True)
+        assert not b3.info()["from_cache"]
+        assert len(json.loads(path.read_text())["plans"]) == 2
+        b4 = sp.Batch(bases, frames, "svd_exhaustive", "fp16", autotune=True)   # no kernel choice: own key
+        assert not b4.info()["from_cache"] and b4.info()["proj_variant"] == 0
+    finally:
+        sp.set_tune_cache(None)
