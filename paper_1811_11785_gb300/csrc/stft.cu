@@ -5,7 +5,9 @@
 // N/2-point complex FFT of z[j] = (w x)[2j] + i (w x)[2j + 1] (radix-2 Stockham in shared
 // memory, natural order out), followed by X[k] = E[k] + exp(-2 pi i k / N) O[k] with
 // E[k] = (Z[k] + conj(Z[N/2 - k])) / 2 and O[k] = (Z[k] - conj(Z[N/2 - k])) / (2i), the DFTs of
-// the even and odd samples.  A CTA takes `fpc` frames x M channels at a time (persistent grid);
+// the even and odd samples.  For N = 256, 512, 1024 one warp computes a transform with its
+// points in registers (stft_warp_kernel, below); other N use stft_kernel: a CTA takes `fpc`
+// frames x M channels at a time (persistent grid);
 // the samples of a frame are read coalesced from the channel rows, the bins written coalesced
 // in the [T][M][B] layout the localisation calls take; window and twiddles come from tables
 // the CTA computes once in shared memory.
@@ -110,6 +112,180 @@ __global__ void __launch_bounds__(kStftThreads)
     }
 }
 
+// ---------------------------------------------------------------- warp-per-transform FFT
+// For N = 64 P (P = 4, 8, 16: N = 256, 512, 1024) a warp computes one (frame, channel)
+// transform at a time with its n = N/2 = 32 P complex points held P per lane.  With
+// z[n1 + 32 n2] (n1 = lane, n2 < P) and bins k = k2 + P (q + 8 r) (k2 < P, q < 8, r < 4):
+//   stage A  a P-point DFT over n2 in registers, times W_n^(n1 k2)         -> Y[k2][n1]
+//   stage B  8-point DFTs over m of Y[k2][a + 4 m] (a < 4), times W_32^(a q) -> U[k2][a][q]
+//   stage C  4-point DFTs over a of U[k2][a][q]                             -> Z[k2 + P (q + 8 r)]
+// (Cooley-Tukey n = 32 x P, then 32 = 4 x 8), each in-register DFT a radix-2 decimation in
+// frequency whose output sits in bit-reversed order.  Stages exchange data through the warp's
+// own shared-memory buffer (index i stored at i + i / 32), separated by __syncwarp.  Then the
+// real-input post-processing and the store as in stft_kernel.  Window, W_n and the post-
+// processing twiddles come from tables the CTA computes once.
+constexpr int kWarpFftWarps = 8;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 5); }
+
+template <int S>
+__device__ __forceinline__ int bitrev(int i) {
+    int r = 0;
+#pragma unroll
+    for (int b = 1; b < S; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
+    return r;
+}
+
+// In-place S-point DFT (S = 4, 8, 16), radix-2 decimation in frequency; v[i] ends as X[bitrev(i)].
+// w[j] = exp(-2 pi i j / S), j < S / 2.
+template <int S>
+__device__ __forceinline__ void dft_dif(float2 (&v)[S], const float2 (&w)[S / 2]) {
+#pragma unroll
+    for (int h = S / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int s0 = 0; s0 < S; s0 += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const float2 a = v[s0 + j], b = v[s0 + j + h];
+                v[s0 + j] = make_float2(a.x + b.x, a.y + b.y);
+                const float2 d = make_float2(a.x - b.x, a.y - b.y);
+                const int e = j * (S / (2 * h));
+                v[s0 + j + h] = e == 0 ? d : cmul(d, w[e]);
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(32 * kWarpFftWarps)
+    stft_warp_kernel(const float *__restrict__ x, long long ld, int M, int hop, int T, int vec2,
+                     const uint8_t *__restrict__ mask, float2 *__restrict__ out, int *status) {
+    constexpr int n = 32 * P, N = 2 * n, B = n + 1;
+    constexpr int nb = n + n / 32;            // padded per-warp buffer
+    __shared__ float2 buf[kWarpFftWarps][nb];
+    __shared__ float2 wn[n];                  // exp(-2 pi i j / n)
+    __shared__ float2 pt[n + 1];              // exp(-2 pi i k / N)
+    __shared__ float2 win2[n];                // (w[2j], w[2j + 1])
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float s_, c_;
+        sincospif(-2.f * (float)j / (float)n, &s_, &c_);
+        wn[j] = make_float2(c_, s_);
+        win2[j] = make_float2(sinpif(((float)(2 * j) + 0.5f) / (float)N), sinpif(((float)(2 * j + 1) + 0.5f) / (float)N));
+    }
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+        float s_, c_;
+        sincospif(-2.f * (float)k / (float)N, &s_, &c_);
+        pt[k] = make_float2(c_, s_);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *sb = buf[warp];
+    // per-lane constants: the small DFTs' twiddles and stage A's W_n^(lane k2)
+    float2 wP[P / 2], w8[4], w4[2], tA[P];
+#pragma unroll
+    for (int j = 0; j < P / 2; ++j) wP[j] = wn[j * (n / P)];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w8[j] = wn[j * (n / 8)];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) w4[j] = wn[j * (n / 4)];
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) tA[k2] = wn[(lane * k2) % n];
+    const long long n_tasks = (long long)T * M;
+    for (long long task = (long long)blockIdx.x * kWarpFftWarps + warp; task < n_tasks;
+         task += (long long)gridDim.x * kWarpFftWarps) {
+        const long long t = task / M;
+        const int m = (int)(task % M);
+        const float *row = x + (size_t)m * ld + (size_t)t * hop;
+        // ---- stage A
+        float2 v[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int j = lane + 32 * q;
+            float2 xv = make_float2(0.f, 0.f);
+            if (!dcheck(t * hop + 2 * j + 1 < ld, status)) {
+            } else if (vec2) {
+                xv = __ldg(reinterpret_cast<const float2 *>(row) + j);
+            } else {
+                xv = make_float2(__ldg(row + 2 * j), __ldg(row + 2 * j + 1));
+            }
+            const float2 wv = win2[j];
+            v[q] = make_float2(wv.x * xv.x, wv.y * xv.y);
+        }
+        dft_dif<P>(v, wP);
+        __syncwarp();   // the previous task's reads of the buffer are done
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int k2 = bitrev<P>(i);
+            sb[pidx(k2 * 32 + lane)] = k2 == 0 ? v[i] : cmul(v[i], tA[k2]);
+        }
+        __syncwarp();
+        // ---- stage B: tasks (k2, a), 4 P of them, P / 8 per lane (P = 4: lanes < 16)
+        constexpr int NB = (4 * P + 31) / 32;
+        float2 u[NB][8];
+        int tb[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            tb[r] = lane + 32 * r;
+            const int k2 = tb[r] >> 2, a = tb[r] & 3;
+#pragma unroll
+            for (int mm = 0; mm < 8; ++mm) u[r][mm] = tb[r] < 4 * P ? sb[pidx(k2 * 32 + a + 4 * mm)] : make_float2(0.f, 0.f);
+            dft_dif<8>(u[r], w8);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            if (tb[r] < 4 * P) {
+                const int k2 = tb[r] >> 2, a = tb[r] & 3;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int q = bitrev<8>(i);
+                    // U[k2][a][q] at (k2 * 8 + q) * 4 + a
+                    sb[pidx((k2 * 8 + q) * 4 + a)] = (a * q) == 0 ? u[r][i] : cmul(u[r][i], wn[(a * q) * (n / 32)]);
+                }
+            }
+        }
+        __syncwarp();
+        // ---- stage C: tasks (k2, q), 8 P of them, P / 4 per lane
+        constexpr int NC = P / 4;
+        float2 c4[NC][4];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            const int tc = lane + 32 * r;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) c4[r][a] = sb[pidx(tc * 4 + a)];
+            dft_dif<4>(c4[r], w4);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < NC; ++r) {
+            const int tc = lane + 32 * r, k2 = tc >> 3, q = tc & 7;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sb[pidx(k2 + P * (q + 8 * bitrev<4>(i)))] = c4[r][i];
+        }
+        __syncwarp();
+        // ---- real-input post-processing and the store
+        const uint8_t *mrow = mask ? mask + (size_t)t * B : nullptr;
+        float2 *orow = out + ((size_t)t * M + m) * B;
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+            const int k = lane + 32 * i;
+            if (k < B) {
+                const float2 zk = sb[pidx(k == n ? 0 : k)];
+                const float2 zr = sb[pidx(k == 0 ? 0 : n - k)];
+                const float2 E = make_float2(0.5f * (zk.x + zr.x), 0.5f * (zk.y - zr.y));
+                const float2 O = make_float2(0.5f * (zk.y + zr.y), -0.5f * (zk.x - zr.x));
+                const float2 w = pt[k];
+                float2 X = make_float2(E.x + w.x * O.x - w.y * O.y, E.y + w.x * O.y + w.y * O.x);
+                if (mrow && mrow[k] == 0) X = make_float2(0.f, 0.f);
+                orow[k] = X;
+            }
+        }
+    }
+}
+
 __global__ void mask_kernel(const float2 *__restrict__ in, long long T, int M, int B, const uint8_t *__restrict__ mask,
                             float2 *__restrict__ out) {
     const long long total = T * M * B;
@@ -140,6 +316,23 @@ int check_stft_args(const float *x, int M, long long n_samples, long long ld, in
 int launch_stft(const float *x, long long ld, int M, int N, int hop, int T, const uint8_t *mask, void *frames,
                 cudaStream_t s) {
     if (T == 0) return SP_OK;
+    if (N == 256 || N == 512 || N == 1024) {   // one warp per transform, points in registers
+        int *status = nullptr;
+        SP_TRY(device_status_ptr(&status));
+        const int vec2 = ((reinterpret_cast<uintptr_t>(x) & 7) == 0 && (ld & 1) == 0 && (hop & 1) == 0) ? 1 : 0;
+        const long long tasks = (long long)T * M;
+        const unsigned grid = (unsigned)std::min<long long>((tasks + kWarpFftWarps - 1) / kWarpFftWarps,
+                                                            8LL * num_sms());
+        const int th = 32 * kWarpFftWarps;
+        if (N == 256)
+            stft_warp_kernel<4><<<grid, th, 0, s>>>(x, ld, M, hop, T, vec2, mask, (float2 *)frames, status);
+        else if (N == 512)
+            stft_warp_kernel<8><<<grid, th, 0, s>>>(x, ld, M, hop, T, vec2, mask, (float2 *)frames, status);
+        else
+            stft_warp_kernel<16><<<grid, th, 0, s>>>(x, ld, M, hop, T, vec2, mask, (float2 *)frames, status);
+        SP_CUDA(cudaGetLastError());
+        return SP_OK;
+    }
     const int n = N / 2;
     int lg_n = 0;
     while ((1 << lg_n) < n) ++lg_n;
