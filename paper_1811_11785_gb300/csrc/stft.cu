@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kStftThreads)
 //   stage C  4-point DFTs over a of U[k2][a][q]                             -> Z[k2 + P (q + 8 r)]
 // (Cooley-Tukey n = 32 x P, then 32 = 4 x 8), each in-register DFT a radix-2 decimation in
 // frequency whose output sits in bit-reversed order.  Stages exchange data through the warp's
-// own shared-memory buffer (index i stored at i + i / 32), separated by __syncwarp.  Then the
+// own shared-memory buffer (swizzled layouts, below), separated by __syncwarp.  Then the
 // real-input post-processing and the store as in stft_kernel.  Window, W_n and the post-
 // processing twiddles come from tables the CTA computes once.
 constexpr int kWarpFftWarps = 8;
@@ -129,7 +129,13 @@ constexpr int kWarpFftWarps = 8;
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 5); }
+// Shared-memory layouts of the three exchanges, XOR-swizzled so that every warp access of
+// the stages (rows of a stage's writes, columns of the next stage's reads) touches each
+// 8-byte bank pair at most twice, the minimum for 32 lanes x 8 bytes:
+//   Y[k2][n1] (stage A out, B in), U[k2][a][q] (B out, C in), Z[k] (C out, post-processing in)
+__device__ __forceinline__ int yidx(int k2, int n1) { return k2 * 32 + (n1 ^ ((k2 & 3) << 2)); }
+__device__ __forceinline__ int uidx(int k2, int a, int q) { return k2 * 32 + ((4 * q + a) ^ (5 * (k2 & 3))); }
+__device__ __forceinline__ int zidx(int k) { return k ^ (((k >> 4) & 3) << 2); }
 
 template <int S>
 __device__ __forceinline__ int bitrev(int i) {
@@ -160,12 +166,11 @@ __device__ __forceinline__ void dft_dif(float2 (&v)[S], const float2 (&w)[S / 2]
 }
 
 template <int P>
-__global__ void __launch_bounds__(32 * kWarpFftWarps)
+__global__ void __launch_bounds__(32 * kWarpFftWarps, P <= 8 ? 3 : 2)
     stft_warp_kernel(const float *__restrict__ x, long long ld, int M, int hop, int T, int vec2,
                      const uint8_t *__restrict__ mask, float2 *__restrict__ out, int *status) {
     constexpr int n = 32 * P, N = 2 * n, B = n + 1;
-    constexpr int nb = n + n / 32;            // padded per-warp buffer
-    __shared__ float2 buf[kWarpFftWarps][nb];
+    __shared__ float2 buf[kWarpFftWarps][n];
     __shared__ float2 wn[n];                  // exp(-2 pi i j / n)
     __shared__ float2 pt[n + 1];              // exp(-2 pi i k / N)
     __shared__ float2 win2[n];                // (w[2j], w[2j + 1])
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float2 *sb = buf[warp];
     // per-lane constants: the small DFTs' twiddles and stage A's W_n^(lane k2)
-    float2 wP[P / 2], w8[4], w4[2], tA[P];
+    float2 wP[P / 2], w8[4], w4[2], tA[P], tB[8];
 #pragma unroll
     for (int j = 0; j < P / 2; ++j) wP[j] = wn[j * (n / P)];
 #pragma unroll
@@ -193,33 +198,46 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
     for (int j = 0; j < 2; ++j) w4[j] = wn[j * (n / 4)];
 #pragma unroll
     for (int k2 = 0; k2 < P; ++k2) tA[k2] = wn[(lane * k2) % n];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tB[q] = wn[((lane & 3) * q) * (n / 32)];   // W_32^(a q), a = lane mod 4
     const long long n_tasks = (long long)T * M;
-    for (long long task = (long long)blockIdx.x * kWarpFftWarps + warp; task < n_tasks;
-         task += (long long)gridDim.x * kWarpFftWarps) {
-        const long long t = task / M;
-        const int m = (int)(task % M);
-        const float *row = x + (size_t)m * ld + (size_t)t * hop;
-        // ---- stage A
-        float2 v[P];
+    const long long stride = (long long)gridDim.x * kWarpFftWarps;
+    // the samples of task tk (raw, unwindowed), loaded one task ahead of the transform
+    auto load = [&](long long tk, float2 (&r)[P]) {
+        const long long tt = tk / M;
+        const int mm = (int)(tk % M);
+        const float *row = x + (size_t)mm * ld + (size_t)tt * hop;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int j = lane + 32 * q;
-            float2 xv = make_float2(0.f, 0.f);
-            if (!dcheck(t * hop + 2 * j + 1 < ld, status)) {
+            r[q] = make_float2(0.f, 0.f);
+            if (tk >= n_tasks || !dcheck(tt * hop + 2 * j + 1 < ld, status)) {
             } else if (vec2) {
-                xv = __ldg(reinterpret_cast<const float2 *>(row) + j);
+                r[q] = __ldg(reinterpret_cast<const float2 *>(row) + j);
             } else {
-                xv = make_float2(__ldg(row + 2 * j), __ldg(row + 2 * j + 1));
+                r[q] = make_float2(__ldg(row + 2 * j), __ldg(row + 2 * j + 1));
             }
-            const float2 wv = win2[j];
-            v[q] = make_float2(wv.x * xv.x, wv.y * xv.y);
         }
+    };
+    float2 nxt[P];
+    load((long long)blockIdx.x * kWarpFftWarps + warp, nxt);
+    for (long long task = (long long)blockIdx.x * kWarpFftWarps + warp; task < n_tasks; task += stride) {
+        const long long t = task / M;
+        const int m = (int)(task % M);
+        // ---- stage A (the window applied to the prefetched samples; the next task's loads go out)
+        float2 v[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float2 wv = win2[lane + 32 * q];
+            v[q] = make_float2(wv.x * nxt[q].x, wv.y * nxt[q].y);
+        }
+        load(task + stride, nxt);
         dft_dif<P>(v, wP);
         __syncwarp();   // the previous task's reads of the buffer are done
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const int k2 = bitrev<P>(i);
-            sb[pidx(k2 * 32 + lane)] = k2 == 0 ? v[i] : cmul(v[i], tA[k2]);
+            sb[yidx(k2, lane)] = k2 == 0 ? v[i] : cmul(v[i], tA[k2]);
         }
         __syncwarp();
         // ---- stage B: tasks (k2, a), 4 P of them, P / 8 per lane (P = 4: lanes < 16)
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
             tb[r] = lane + 32 * r;
             const int k2 = tb[r] >> 2, a = tb[r] & 3;
 #pragma unroll
-            for (int mm = 0; mm < 8; ++mm) u[r][mm] = tb[r] < 4 * P ? sb[pidx(k2 * 32 + a + 4 * mm)] : make_float2(0.f, 0.f);
+            for (int mm = 0; mm < 8; ++mm) u[r][mm] = tb[r] < 4 * P ? sb[yidx(k2, a + 4 * mm)] : make_float2(0.f, 0.f);
             dft_dif<8>(u[r], w8);
         }
         __syncwarp();
@@ -242,8 +260,7 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int q = bitrev<8>(i);
-                    // U[k2][a][q] at (k2 * 8 + q) * 4 + a
-                    sb[pidx((k2 * 8 + q) * 4 + a)] = (a * q) == 0 ? u[r][i] : cmul(u[r][i], wn[(a * q) * (n / 32)]);
+                    sb[uidx(k2, a, q)] = (a * q) == 0 ? u[r][i] : cmul(u[r][i], tB[q]);
                 }
             }
         }
@@ -255,7 +272,7 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
         for (int r = 0; r < NC; ++r) {
             const int tc = lane + 32 * r;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) c4[r][a] = sb[pidx(tc * 4 + a)];
+            for (int a = 0; a < 4; ++a) c4[r][a] = sb[uidx(tc >> 3, a, tc & 7)];
             dft_dif<4>(c4[r], w4);
         }
         __syncwarp();
@@ -263,7 +280,7 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
         for (int r = 0; r < NC; ++r) {
             const int tc = lane + 32 * r, k2 = tc >> 3, q = tc & 7;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) sb[pidx(k2 + P * (q + 8 * bitrev<4>(i)))] = c4[r][i];
+            for (int i = 0; i < 4; ++i) sb[zidx(k2 + P * (q + 8 * bitrev<4>(i)))] = c4[r][i];
         }
         __syncwarp();
         // ---- real-input post-processing and the store
@@ -273,8 +290,8 @@ __global__ void __launch_bounds__(32 * kWarpFftWarps)
         for (int i = 0; i <= P; ++i) {
             const int k = lane + 32 * i;
             if (k < B) {
-                const float2 zk = sb[pidx(k == n ? 0 : k)];
-                const float2 zr = sb[pidx(k == 0 ? 0 : n - k)];
+                const float2 zk = sb[zidx(k == n ? 0 : k)];
+                const float2 zr = sb[zidx(k == 0 ? 0 : n - k)];
                 const float2 E = make_float2(0.5f * (zk.x + zr.x), 0.5f * (zk.y - zr.y));
                 const float2 O = make_float2(0.5f * (zk.y + zr.y), -0.5f * (zk.x - zr.x));
                 const float2 w = pt[k];
