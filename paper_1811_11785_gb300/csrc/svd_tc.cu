@@ -784,6 +784,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
     uint64_t *drain = bars + 4 * kRing;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4 * kRing + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 4 * kRing + 2);
+    uint64_t *zbar = bars + 4 * kRing + 3;
     const long long budget = g_wait_budget;
     const int K = prm.K;
 
@@ -795,6 +796,7 @@ __global__ void __launch_bounds__(kScanThreads, 2)
             ptx::mbar_init(&t2_empty[i], 32 * kScanEpiWarps);
         }
         ptx::mbar_init(drain, 1);
+        ptx::mbar_init(zbar, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -813,9 +815,34 @@ __global__ void __launch_bounds__(kScanThreads, 2)
         ptx::tmem_relinquish();
     }
     __syncthreads();
-    // A operand: Z rounded to FP16/BF16, [128 frames][k2] in the 128-byte swizzle layout
-    // (8 loads in flight per thread)
-    {
+    // A operand: Z rounded to FP16/BF16, [128 frames][k2] in the 128-byte swizzle layout.  A tile
+    // of consecutive frames is one contiguous run of Z: one bulk copy into the (still idle) D
+    // ring, then converted from shared memory; listed frames are gathered (8 loads in flight
+    // per thread).
+    const int n_r = (int)min((long long)128, (long long)n_pos - t0);
+    const unsigned z_bytes = (unsigned)n_r * (unsigned)K * 8u;
+    const bool z_bulk = !prm.rows && (z_bytes & 15u) == 0 && z_bytes <= (unsigned)(kRing * b2_bytes);
+    if (z_bulk) {
+        if (tid == 0) {
+            ptx::mbar_arrive_expect_tx(zbar, z_bytes);
+            ptx::bulk_load(smem + off_b2, prm.Z + (size_t)t0 * K, z_bytes, zbar);
+        }
+        if (!ptx::mbar_wait(zbar, 0, budget)) {
+            if (tid == 0) {
+                *abort_flag = 1;
+                atomicOr(&g_status, 1);
+            }
+            ptx::mbar_wait(zbar, 0, kDrainBudget);   // the copy must land before the ring is reused
+        }
+        const float2 *zs = reinterpret_cast<const float2 *>(smem + off_b2);
+        const int per_row = k2_atoms * kAtomElems / 2;
+        for (int e = tid; e < 128 * per_row; e += kScanThreads) {
+            const int r = e / per_row, kk = e % per_row, n = 2 * kk;
+            const float2 z = (r < n_r && kk < K) ? zs[r * K + kk] : make_float2(0.f, 0.f);
+            *reinterpret_cast<uint32_t *>(smem + (n >> 6) * kAtomBytes + ptx::sw128_offset(r, n & 63)) =
+                pack2<BF16>(z.x, z.y);
+        }
+    } else {
         const int per_row = k2_atoms * kAtomElems / 2;
         const int n_el = 128 * per_row;
         for (int e0 = tid; e0 < n_el; e0 += 8 * kScanThreads) {
@@ -1288,7 +1315,7 @@ static ProjKernel proj_kernel_for(const TcLayout &t, int bf, int M) {
 // D tiles in flight of the scan: four, two when the Z tile and four D tiles would not fit (2K > 256)
 static int scan_smem_bytes(const TcLayout &t, int ring) {
     return t.k2_atoms * kAtomBytes + ring * t.k2_atoms * kN2 * 128 + 2 * 128 * kCap * 4 + 128 * 4 +
-           (4 * ring + 3) * 8 + 1024;
+           (4 * ring + 4) * 8 + 1024;
 }
 static int scan_ring_for(const TcLayout &t) {
     return scan_smem_bytes(t, kRingMax) <= 232448 ? kRingMax : 2;
