@@ -303,3 +303,43 @@ def test_wide_basis_inference_and_search():
     ei, _, _ = sp.localize(b, d["frames"], "svd_exhaustive", "fp16")
     torch.cuda.synchronize()
     assert bool(fb.all()) and torch.equal(li, ei)
+
+
+def test_learned_search_on_a_wide_basis():
+    """The 16-mic N = 1024 array (K = 131-135, 2K = 262-270: rows of 33-34 16-byte pieces, the
+    screening with two rows in flight per lane group) with 42 cells of ~15 directions: with a
+    confident network and no fallback, the search matches the oracle's search wherever its
+    cell choice and winner are clear, and its scores are within the FP32 tolerance."""
+    d = _setup("ball16_n1024_q642", 200)
+    cells = I.icosphere(1)
+    cell_of = OL.child_cells(d["wl"]["dirs"], cells)
+    kids = OL.children(cell_of, cells.shape[0])
+    b = oracle_basis_in_library(d)
+    p = sp.Proposal(b, cells, seed=1)
+    assert p.F == 2 * d["ob"]["K"] and p.F > 4 * 48 and np.array_equal(p.cells(), cell_of)
+    params = _params(p, 51)
+    params[-(p.H2 * p.C + p.C):] *= 8.0
+    p.set_params(params)
+    ref_lg = _oracle_logits(p, params, d["Z"])
+    n_top = 4
+    idx, score, proj, fb = p.localize(d["frames"], "fp16", n_top=n_top, theta=0.0)
+    torch.cuda.synchronize()
+    sp.check_status()
+    idx, proj, fb = idx.cpu().numpy(), proj.cpu().numpy(), fb.cpu().numpy()
+    assert not fb.any()
+    oi, obest, ofb = OL.learned_search(d["ob"]["D"], d["Z"], ref_lg, kids, n_top, 0.0)
+    cls, L, Ysvd = d["cls"], d["L"], d["Ysvd"]
+    srt = -np.sort(-ref_lg, axis=1)
+    cells_clear = srt[:, n_top - 1] - srt[:, n_top] > 0.02
+    margin = np.empty(len(idx))
+    for t in range(len(idx)):
+        cand = np.concatenate([kids[c] for c in OL.top_cells(ref_lg, n_top)[t]])
+        y = Ysvd[t, cand]
+        other = y[cls[cand] != cls[oi[t]]]
+        margin[t] = (obest[t] - (other.max() if other.size else -np.inf)) / L
+    ok = cells_clear & (margin > 1e-4)
+    assert ok.mean() > 0.3
+    assert np.all(cls[idx[ok]] == cls[oi[ok]])
+    assert np.max(np.abs(proj[ok] - obest[ok])) <= 2e-3 * L
+    sref = O.score_row(d["tau"], idx, d["X"], d["wl"]["N"])
+    assert np.max(np.abs(score.cpu().numpy() - sref)) <= 1e-5 * L
