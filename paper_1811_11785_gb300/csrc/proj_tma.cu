@@ -27,9 +27,12 @@
 // Fifteen warps leave every thread 128 registers (a scheduler holds at most four warps).
 // V arrives in three stages where shared memory allows (two for wide bases): every SM reads the
 // same 2.4 MB of V in the same chunk order, and its L2 latency, not the STFT's, is the one the
-// third stage hides (measured 336 -> 313 us per 65,536 frames).  What bounds the kernel then
-// is the TMA path for the STFT slices: rows of 32-80 bytes, about 3.5-4.2 TB/s even when the
-// slices are resident in L2.
+// third stage hides (measured 336 -> 313 us per 65,536 frames).  Two paths of about the same
+// length then bound the kernel and overlap well: the STFT slices by TMA (rows of 32-80 bytes;
+// 278 us on their own, 3.4-4.2 TB/s even from L2) and the producer / MMA pipeline around
+// tensor memory (298 us without any STFT load; 230 us without the MMAs as well, 214 us
+// without the producers' PHAT work and tensor-memory stores instead).  Two accumulators taking
+// alternate K16 steps changed nothing (315 us), so it is not the accumulation chain.
 //
 // Every mbarrier wait is bounded; a wait that gives up records an error in the status word
 // and the CTA drains its in-flight TMA loads and MMAs before it frees tensor memory.
