@@ -17,7 +17,7 @@ k-d tree on 2^20 frames); 256 batched streams in one CUDA-graph launch.  --only 
 minutes of basis set-up): the 16-mic, N = 1024 array on the level-6 grid (Q = 40,962).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec fp16|bf16]
-                [--frames T] [--no-extras] [--only array3d|batched|c5] [--array3d-frames T]
+                [--frames T] [--no-extras] [--only array3d|batched|batched_default|c5|samples|sweep|kdtree] [--array3d-frames T]
 Under torchrun each rank localises its own 65,536 frames (weak scaling, no collective on the
 data path); rank 0 prints one JSON line.
 """
@@ -596,6 +596,10 @@ def bench_batched(sp, I, torch, full=False):
         finally:
             sp.set_tune_cache(None)
     g_rate = _rate(bt.run, 10, total, torch)
+    bt_g = sp.Batch(sb, sf, "svd_exhaustive", "fp16", group=True)   # the streams of a basis as one call
+    grouped_rate = _rate(bt_g.run, 10, total, torch)
+    grouped_info = bt_g.info()
+    del bt_g
 
     def serial():   # FP32 where a basis has no tensor-core plan, as in the graph
         for b, f in zip(sb, sf):
@@ -609,6 +613,7 @@ def bench_batched(sp, I, torch, full=False):
                         f"Q {'/'.join(map(str, qs))}, N {'/'.join(map(str, ns))}, K {ks[0]}-{ks[-1]}), "
                         f"50-2000 frames per stream",
             "graph_frames_per_s": g_rate, "serial_frames_per_s": s_rate, "plan": bt.info(),
+            "grouped_plan_frames_per_s": grouped_rate, "grouped_plan": grouped_info,
             "basis_setup_s": setup_s, "autotune_s": tune_s, "plan_from_cache_s": cached_s,
             "plan_from_cache": cached}
 
@@ -635,7 +640,8 @@ def main():
     ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16"])
     ap.add_argument("--frames", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the SRP / precision comparison lines")
-    ap.add_argument("--only", choices=["array3d", "batched", "c5", "samples", "sweep", "kdtree"], default=None,
+    ap.add_argument("--only", choices=["array3d", "batched", "batched_default", "c5", "samples", "sweep", "kdtree"],
+                    default=None,
                     help="run only one extra section and print its JSON (profiling runs)")
     ap.add_argument("--array3d-frames", type=int, default=C4_UNIQUE,
                     help="unique frames of the 3-D array section (repeated to 2^20 unless --only)")
@@ -669,6 +675,8 @@ def main():
             print(json.dumps(bench_delta_sweep(sp, I, torch)), flush=True)
         elif args.only == "kdtree":
             print(json.dumps(bench_kdtree(sp, I, torch)), flush=True)
+        elif args.only == "batched_default":
+            print(json.dumps(bench_batched(sp, I, torch)), flush=True)
         else:
             print(json.dumps(bench_batched(sp, I, torch, full=True)), flush=True)
         return

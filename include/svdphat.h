@@ -379,19 +379,30 @@ int sp_set_wait_budget(long long iterations);
  * arguments, per stream as sp_localize; a tune cache that exists but does not parse), SP_ECUDA.
  * sp_batch_run: one graph launch on stream (asynchronous).
  * sp_batch_info: the chosen shape (proj_variant 0: TMA-fed GEMM1 where it applies, 1:
- * register-fed), the measured milliseconds of one launch (autotuned plans, else 0), how many
- * streams run in FP32, and whether the shape came from the tune cache.  Any out pointer may
- * be NULL.
+ * register-fed; grouped 1: the groups below are localised one call each), the measured
+ * milliseconds of one launch (autotuned plans, else 0), how many streams run in FP32, whether
+ * the shape came from the tune cache, and how many groups the plan formed.  Any out pointer
+ * may be NULL.
+ * Groups: streams with the same basis and precision whose frames start on a 16-byte boundary
+ * (at most 2^28 frames per group) form a group.  A grouped plan copies a group's frames into
+ * one buffer the plan owns, runs one sp_localize-equivalent call on it and copies the results
+ * back to each stream's outputs: the same kernels on the same frames, so every stream's
+ * results stay bit-identical to its own sp_localize call, while the GPU sees a few large
+ * launches instead of many small ones.  The plan holds the copy (as many bytes as the grouped
+ * streams' frames).  Autotuned plans try both forms; other plans group only with
+ * SP_BATCH_GROUP.  (On the bench's mix of 256 streams of 50-2000 frames over 16 bases the
+ * per-stream form was the faster: the copies cost more than the launches they save.)
  * sp_localize_batched: create (no autotuning), run once, synchronise, destroy.
  * ================================================================================= */
 #define SP_BATCH_AUTOTUNE 1
 #define SP_BATCH_TUNE_KERNELS 2
+#define SP_BATCH_GROUP 4
 int sp_batch_create(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
                     sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
                     float *const *proj_dev, int flags, void *stream, sp_batch **out);
 int sp_batch_run(sp_batch *bt, void *stream);
 int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, int *proj_variant, float *ms,
-                  int *n_fp32, int *from_cache);
+                  int *n_fp32, int *from_cache, int *grouped, int *n_groups);
 void sp_batch_destroy(sp_batch *bt);
 int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *frames_dev, const int *T,
                         sp_mode mode, sp_prec prec, int32_t *const *idx_dev, float *const *score_dev,
@@ -399,17 +410,19 @@ int sp_localize_batched(int n, const sp_basis *const *bases, const void *const *
 
 /* The autotune cache (host only; no device call): path of a JSON file holding
  * {"format": "svdphat-tune-cache", "version": 1, "plans": {key: {"branches": b,
- * "tiles_per_cta": t, "proj_variant": v, "ms": m}}}; NULL or "" disables it (the default).
+ * "tiles_per_cta": t, "proj_variant": v, "grouped": g, "ms": m}}} ("grouped" may be absent:
+ * 0); NULL or "" disables it (the default).
  * The file is created on the first store and rewritten whole through a temporary file and
  * a rename; a file that exists but does not parse is never overwritten (SP_EINVAL).
  * sp_tune_cache_get: *found = 1 and the stored shape if key is present, else *found = 0
  * (out pointers other than found may be NULL).  sp_tune_cache_put: stores or replaces an
- * entry (branches >= 1, tiles_per_cta in {1, 2, 4}, proj_variant in {0, 1}, ms >= 0).
+ * entry (branches >= 1, tiles_per_cta in {1, 2, 4}, proj_variant in {0, 1}, grouped in {0, 1},
+ * ms >= 0).
  * Keys: 1-512 printable ASCII characters without '"' or '\'.  Errors: SP_EINVAL. */
 int sp_set_tune_cache(const char *path);
 int sp_tune_cache_get(const char *key, int *branches, int *tiles_per_cta, int *proj_variant, float *ms,
-                      int *found);
-int sp_tune_cache_put(const char *key, int branches, int tiles_per_cta, int proj_variant, float ms);
+                      int *grouped, int *found);
+int sp_tune_cache_put(const char *key, int branches, int tiles_per_cta, int proj_variant, float ms, int grouped);
 
 /* =================================================================================
  * Learned direction proposal (no counterpart in the paper).  The paper searches Eq. 14

@@ -78,10 +78,11 @@ _SIGS = {
     "sp_batch_create": ([ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
                          ctypes.POINTER(_vp)], ctypes.c_int),
     "sp_batch_run": ([_vp, _vp], ctypes.c_int),
-    "sp_batch_info": ([_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float), _ip, _ip], ctypes.c_int),
+    "sp_batch_info": ([_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float), _ip, _ip, _ip, _ip], ctypes.c_int),
     "sp_set_tune_cache": ([ctypes.c_char_p], ctypes.c_int),
-    "sp_tune_cache_get": ([ctypes.c_char_p, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float), _ip], ctypes.c_int),
-    "sp_tune_cache_put": ([ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float], ctypes.c_int),
+    "sp_tune_cache_get": ([ctypes.c_char_p, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float), _ip, _ip], ctypes.c_int),
+    "sp_tune_cache_put": ([ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int],
+                          ctypes.c_int),
     "sp_batch_destroy": ([_vp], None),
     "sp_localize_batched": ([ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
                             ctypes.c_int),
@@ -501,18 +502,20 @@ def set_tune_cache(path) -> None:
 
 def tune_cache_get(key: str):
     """sp_tune_cache_get: the stored shape dict for key, or None."""
-    br, tpc, pv, found = (ctypes.c_int() for _ in range(4))
+    br, tpc, pv, gr, found = (ctypes.c_int() for _ in range(5))
     ms = ctypes.c_float()
     _check("sp_tune_cache_get", lib().sp_tune_cache_get(key.encode(), ctypes.byref(br), ctypes.byref(tpc),
-                                                        ctypes.byref(pv), ctypes.byref(ms), ctypes.byref(found)))
+                                                        ctypes.byref(pv), ctypes.byref(ms), ctypes.byref(gr),
+                                                        ctypes.byref(found)))
     if not found.value:
         return None
-    return dict(branches=br.value, tiles_per_cta=tpc.value, proj_variant=pv.value, ms=ms.value)
+    return dict(branches=br.value, tiles_per_cta=tpc.value, proj_variant=pv.value, ms=ms.value, grouped=gr.value)
 
 
-def tune_cache_put(key: str, branches: int, tiles_per_cta: int, proj_variant: int, ms: float) -> None:
+def tune_cache_put(key: str, branches: int, tiles_per_cta: int, proj_variant: int, ms: float,
+                   grouped: int = 0) -> None:
     _check("sp_tune_cache_put", lib().sp_tune_cache_put(key.encode(), int(branches), int(tiles_per_cta),
-                                                        int(proj_variant), float(ms)))
+                                                        int(proj_variant), float(ms), int(grouped)))
 
 
 class Proposal:
@@ -645,7 +648,7 @@ class Batch:
     tensors, one per stream)."""
 
     def __init__(self, bases, frames, mode="svd_exhaustive", prec="fp16", score=True, proj=True, autotune=False,
-                 tune_kernels=False):
+                 tune_kernels=False, group=False):
         import torch
         n = len(bases)
         if len(frames) != n:
@@ -663,19 +666,20 @@ class Batch:
         _check("sp_batch_create", lib().sp_batch_create(
             n, bh, _ptr_array(frames), Ta, _mode(mode), _prec(prec), _ptr_array(self.idx),
             _ptr_array(self.score) if score else None, _ptr_array(self.proj) if proj else None,
-            (1 if autotune else 0) | (2 if tune_kernels else 0), _stream(), ctypes.byref(h)))
+            (1 if autotune else 0) | (2 if tune_kernels else 0) | (4 if group else 0), _stream(), ctypes.byref(h)))
         self._h = h
 
     def run(self):
         _check("sp_batch_run", lib().sp_batch_run(self._h, _stream()))
 
     def info(self) -> dict:
-        br, tpc, pv, nf, fc = (ctypes.c_int() for _ in range(5))
+        br, tpc, pv, nf, fc, gr, ng = (ctypes.c_int() for _ in range(7))
         ms = ctypes.c_float()
         _check("sp_batch_info", lib().sp_batch_info(self._h, ctypes.byref(br), ctypes.byref(tpc), ctypes.byref(pv),
-                                                    ctypes.byref(ms), ctypes.byref(nf), ctypes.byref(fc)))
+                                                    ctypes.byref(ms), ctypes.byref(nf), ctypes.byref(fc),
+                                                    ctypes.byref(gr), ctypes.byref(ng)))
         return dict(branches=br.value, tiles_per_cta=tpc.value, proj_variant=pv.value, ms=ms.value,
-                    n_fp32=nf.value, from_cache=bool(fc.value))
+                    n_fp32=nf.value, from_cache=bool(fc.value), grouped=bool(gr.value), n_groups=ng.value)
 
     def __del__(self):
         h = getattr(self, "_h", None)

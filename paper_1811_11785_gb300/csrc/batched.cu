@@ -20,7 +20,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <memory>
+#include <utility>
 #include <new>
 #include <string>
 #include <vector>
@@ -46,6 +48,18 @@ struct sp_batch {
     int branches = 0, tiles_per_cta = 1, proj_variant = 0;
     float ms = 0.f;                     // measured time of one launch (autotuned plans)
     int from_cache = 0;                 // the shape came from the tune cache
+    // Groups: streams that share a basis, a precision and 16-byte-aligned frames (two or more
+    // each).  A grouped plan copies a group's frames into one buffer, localises them with one
+    // call and copies the results back; `solo` lists the streams in no group.
+    struct Group {
+        std::vector<int> members;
+        int T = 0;
+        bool want_score = false, want_proj = false;
+        std::unique_ptr<sp::DevBuf> frames, out, work;
+    };
+    std::vector<Group> groups;
+    std::vector<int> solo;
+    int grouped = 0;                    // the plan runs the groups (1) or every stream alone (0)
     ~sp_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         for (auto s : side) cudaStreamDestroy(s);
@@ -63,6 +77,37 @@ int enqueue_stream(sp_batch *bt, int i, cudaStream_t s, int tiles_per_cta, int p
     const int cap = std::max(1, (tiles + tiles_per_cta - 1) / tiles_per_cta);
     return localize_ws(bt->b[i], bt->frames[i], bt->T[i], bt->mode, bt->prec[i], bt->idx[i], bt->score[i],
                        bt->proj[i], s, *bt->work[i], cap, proj_variant);
+}
+
+size_t group_out_stride(int T) { return ((size_t)T * 4 + 255) / 256 * 256; }
+
+// A group: its streams' frames into the group buffer, one localisation, the results back.
+int enqueue_group(sp_batch *bt, sp_batch::Group &g, cudaStream_t s, int tiles_per_cta, int proj_variant) {
+    const sp_basis *b = bt->b[g.members[0]];
+    const size_t fb = (size_t)b->st->M * b->st->B * 8;
+    char *gf = g.frames->as<char>();
+    size_t off = 0;
+    for (int i : g.members) {
+        SP_CUDA(cudaMemcpyAsync(gf + off * fb, bt->frames[i], (size_t)bt->T[i] * fb, cudaMemcpyDeviceToDevice, s));
+        off += (size_t)bt->T[i];
+    }
+    const size_t st = group_out_stride(g.T);
+    int32_t *gidx = g.out->as<int32_t>();
+    float *gscore = reinterpret_cast<float *>(g.out->as<char>() + st);
+    float *gproj = reinterpret_cast<float *>(g.out->as<char>() + 2 * st);
+    const int tiles = (g.T + 127) / 128;
+    const int cap = std::max(1, (tiles + tiles_per_cta - 1) / tiles_per_cta);
+    SP_TRY(localize_ws(b, gf, g.T, bt->mode, bt->prec[g.members[0]], gidx, g.want_score ? gscore : nullptr,
+                       g.want_proj ? gproj : nullptr, s, *g.work, cap, proj_variant));
+    off = 0;
+    for (int i : g.members) {
+        const size_t nb = (size_t)bt->T[i] * 4;
+        SP_CUDA(cudaMemcpyAsync(bt->idx[i], gidx + off, nb, cudaMemcpyDeviceToDevice, s));
+        if (bt->score[i]) SP_CUDA(cudaMemcpyAsync(bt->score[i], gscore + off, nb, cudaMemcpyDeviceToDevice, s));
+        if (bt->proj[i]) SP_CUDA(cudaMemcpyAsync(bt->proj[i], gproj + off, nb, cudaMemcpyDeviceToDevice, s));
+        off += (size_t)bt->T[i];
+    }
+    return SP_OK;
 }
 
 // The batch's signature: device, mode, precision, and a 64-bit FNV-1a hash of every stream's
@@ -97,8 +142,9 @@ int plan_key(const sp_batch *bt, std::string *key) {
     return SP_OK;
 }
 
-// Capture every stream's kernels into one graph: stream i on branch i % branches.
-int build_graph(sp_batch *bt, int branches, int tiles_per_cta, int proj_variant, cudaGraphExec_t *out) {
+// Capture the plan's units into one graph: unit u on branch u % branches.  Units: every
+// stream alone, or (grouped) the groups, then the streams in no group.
+int build_graph(sp_batch *bt, int branches, int tiles_per_cta, int proj_variant, int grouped, cudaGraphExec_t *out) {
     *out = nullptr;
     while ((int)bt->side.size() < branches) {
         cudaStream_t s;
@@ -114,8 +160,16 @@ int build_graph(sp_batch *bt, int branches, int tiles_per_cta, int proj_variant,
     if (cudaEventRecord(bt->fork, bt->origin) != cudaSuccess) rc = fail(SP_ECUDA, "batch: fork record");
     for (int k = 0; k < branches && rc == SP_OK; ++k)
         if (cudaStreamWaitEvent(bt->side[k], bt->fork, 0) != cudaSuccess) rc = fail(SP_ECUDA, "batch: fork wait");
-    for (int i = 0; i < bt->n && rc == SP_OK; ++i)
-        rc = enqueue_stream(bt, i, bt->side[i % branches], tiles_per_cta, proj_variant);
+    if (grouped) {
+        int u = 0;
+        for (size_t gi = 0; gi < bt->groups.size() && rc == SP_OK; ++gi, ++u)
+            rc = enqueue_group(bt, bt->groups[gi], bt->side[u % branches], tiles_per_cta, proj_variant);
+        for (size_t k = 0; k < bt->solo.size() && rc == SP_OK; ++k, ++u)
+            rc = enqueue_stream(bt, bt->solo[k], bt->side[u % branches], tiles_per_cta, proj_variant);
+    } else {
+        for (int i = 0; i < bt->n && rc == SP_OK; ++i)
+            rc = enqueue_stream(bt, i, bt->side[i % branches], tiles_per_cta, proj_variant);
+    }
     for (int k = 0; k < branches && rc == SP_OK; ++k) {
         if (cudaEventRecord(bt->join[k], bt->side[k]) != cudaSuccess ||
             cudaStreamWaitEvent(bt->origin, bt->join[k], 0) != cudaSuccess)
@@ -169,7 +223,8 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
     *out = nullptr;
     SP_CHECK(n >= 1 && n <= 65536, SP_EINVAL, "sp_batch_create: n must be in [1, 65536]");
     SP_CHECK(bases && frames_dev && T && idx_dev, SP_EINVAL, "sp_batch_create: null array");
-    SP_CHECK((flags & ~(SP_BATCH_AUTOTUNE | SP_BATCH_TUNE_KERNELS)) == 0, SP_EINVAL, "sp_batch_create: bad flags");
+    SP_CHECK((flags & ~(SP_BATCH_AUTOTUNE | SP_BATCH_TUNE_KERNELS | SP_BATCH_GROUP)) == 0, SP_EINVAL,
+             "sp_batch_create: bad flags");
     SP_CHECK(prec == SP_PREC_FP32 || prec == SP_PREC_FP16 || prec == SP_PREC_BF16, SP_EINVAL,
              "sp_batch_create: bad precision");
     for (int i = 0; i < n; ++i) {
@@ -193,6 +248,50 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
         bt->work.emplace_back(new (std::nothrow) DevBuf());
         SP_CHECK(bt->work.back(), SP_ENOMEM, "sp_batch_create: host allocation failed");
     }
+    {   // groups: streams sharing (basis, precision), frames 16-byte aligned, at most 2^28 frames
+        std::map<std::pair<const sp_basis *, int>, std::vector<int>> by;
+        for (int i = 0; i < n; ++i) {
+            if ((reinterpret_cast<uintptr_t>(frames_dev[i]) & 15) != 0) {
+                bt->solo.push_back(i);   // an unaligned stream takes its own kernels, as sp_localize does
+                continue;
+            }
+            by[std::make_pair(bases[i], (int)bt->prec[i])].push_back(i);
+        }
+        for (auto &kv : by) {
+            std::vector<int> cur;
+            long long Tt = 0;
+            auto flush = [&]() -> int {
+                if (cur.size() == 1) bt->solo.push_back(cur[0]);
+                if (cur.size() >= 2) {
+                    sp_batch::Group g;
+                    g.members = cur;
+                    g.T = (int)Tt;
+                    for (int i : cur) {
+                        g.want_score = g.want_score || bt->score[i] != nullptr;
+                        g.want_proj = g.want_proj || bt->proj[i] != nullptr;
+                    }
+                    g.frames.reset(new (std::nothrow) DevBuf());
+                    g.out.reset(new (std::nothrow) DevBuf());
+                    g.work.reset(new (std::nothrow) DevBuf());
+                    SP_CHECK(g.frames && g.out && g.work, SP_ENOMEM, "sp_batch_create: host allocation failed");
+                    const sp_steering *st = bt->b[cur[0]]->st;
+                    SP_TRY(g.frames->reserve((size_t)Tt * st->M * st->B * 8));
+                    SP_TRY(g.out->reserve(3 * group_out_stride(g.T)));
+                    bt->groups.push_back(std::move(g));
+                }
+                cur.clear();
+                Tt = 0;
+                return SP_OK;
+            };
+            for (int i : kv.second) {
+                if (Tt + T[i] > (1LL << 28)) SP_TRY(flush());
+                cur.push_back(i);
+                Tt += T[i];
+            }
+            SP_TRY(flush());
+        }
+        std::sort(bt->solo.begin(), bt->solo.end());
+    }
     SP_CUDA(cudaStreamCreateWithFlags(&bt->origin, cudaStreamNonBlocking));
     SP_CUDA(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
     // the plan's own stream runs after the work already queued on the caller's stream (which
@@ -202,26 +301,35 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
     // one eager pass: sizes every workspace (no allocation happens while capturing) and
     // sets the kernels' attributes
     for (int i = 0; i < n; ++i) SP_TRY(enqueue_stream(bt.get(), i, bt->origin, 1, 0));
+    for (auto &g : bt->groups) SP_TRY(enqueue_group(bt.get(), g, bt->origin, 1, 0));
     SP_CUDA(cudaStreamSynchronize(bt->origin));
-    std::vector<int> br_cand;
-    for (int k : {8, 32, 128})
-        if (k < n) br_cand.push_back(k);
-    br_cand.push_back(n);
+    const int n_units[2] = {n, (int)(bt->groups.size() + bt->solo.size())};
+    auto br_cand = [&](int gv) {
+        std::vector<int> c;
+        for (int k : {8, 32, 128})
+            if (k < n_units[gv]) c.push_back(k);
+        c.push_back(n_units[gv]);
+        return c;
+    };
+    const int gv_max = bt->groups.empty() ? 0 : 1;
     if (flags & SP_BATCH_AUTOTUNE) {
         std::string key;
-        TunedShape cached{0, 0, 0, 0.f};
+        TunedShape cached{0, 0, 0, 0.f, 0};
         bool found = false;
         if (tune_cache_enabled()) {
             SP_TRY(plan_key(bt.get(), &key));
             key += (flags & SP_BATCH_TUNE_KERNELS) ? "/k" : "";
             if (tune_cache_get(key, &cached, &found) != SP_OK) found = false;   // unreadable file: tune
-            if (found && !(cached.branches >= 1 && cached.branches <= n &&
+            if (found && !(cached.grouped >= 0 && cached.grouped <= gv_max && cached.branches >= 1 &&
+                           cached.branches <= n_units[cached.grouped] &&
                            (cached.tiles_per_cta == 1 || cached.tiles_per_cta == 2 || cached.tiles_per_cta == 4) &&
                            (cached.proj_variant == 0 || cached.proj_variant == 1)))
                 found = false;
         }
         if (found) {
-            SP_TRY(build_graph(bt.get(), cached.branches, cached.tiles_per_cta, cached.proj_variant, &bt->exec));
+            SP_TRY(build_graph(bt.get(), cached.branches, cached.tiles_per_cta, cached.proj_variant, cached.grouped,
+                               &bt->exec));
+            bt->grouped = cached.grouped;
             bt->branches = cached.branches;
             bt->tiles_per_cta = cached.tiles_per_cta;
             bt->proj_variant = cached.proj_variant;
@@ -232,11 +340,12 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
             for (int i = 0; i < n && (flags & SP_BATCH_TUNE_KERNELS); ++i)
                 both = both || (bt->prec[i] != SP_PREC_FP32 && proj_tma_applies(bases[i], frames_dev[i]));
             float best = 0.f;
+            for (int gv = 0; gv <= gv_max; ++gv)
             for (int pv = 0; pv < (both ? 2 : 1); ++pv)
-                for (int br : br_cand)
+                for (int br : br_cand(gv))
                     for (int tpc : {1, 2, 4}) {
                         cudaGraphExec_t ex = nullptr;
-                        SP_TRY(build_graph(bt.get(), br, tpc, pv, &ex));
+                        SP_TRY(build_graph(bt.get(), br, tpc, pv, gv, &ex));
                         float ms = 0.f;
                         const int rc = time_graph(ex, bt->origin, &ms);
                         if (rc != SP_OK) {
@@ -250,18 +359,21 @@ int sp_batch_create(int n, const sp_basis *const *bases, const void *const *fram
                             bt->branches = br;
                             bt->tiles_per_cta = tpc;
                             bt->proj_variant = pv;
+                            bt->grouped = gv;
                         } else {
                             cudaGraphExecDestroy(ex);
                         }
                     }
             bt->ms = best;
             if (!key.empty())
-                SP_TRY(tune_cache_put(key, TunedShape{bt->branches, bt->tiles_per_cta, bt->proj_variant, best}));
+                SP_TRY(tune_cache_put(key, TunedShape{bt->branches, bt->tiles_per_cta, bt->proj_variant, best,
+                                                      bt->grouped}));
         }
     } else {
-        bt->branches = std::min(n, 32);
+        bt->grouped = (flags & SP_BATCH_GROUP) ? gv_max : 0;   // groups only when asked for
+        bt->branches = std::min(n_units[bt->grouped], 32);
         bt->tiles_per_cta = 1;
-        SP_TRY(build_graph(bt.get(), bt->branches, 1, 0, &bt->exec));
+        SP_TRY(build_graph(bt.get(), bt->branches, 1, 0, bt->grouped, &bt->exec));
     }
     *out = bt.release();
     return SP_OK;
@@ -274,8 +386,10 @@ int sp_batch_run(sp_batch *bt, void *stream) {
 }
 
 int sp_batch_info(const sp_batch *bt, int *branches, int *tiles_per_cta, int *proj_variant, float *ms, int *n_fp32,
-                  int *from_cache) {
+                  int *from_cache, int *grouped, int *n_groups) {
     SP_CHECK(bt, SP_EINVAL, "sp_batch_info: null plan");
+    if (grouped) *grouped = bt->grouped;
+    if (n_groups) *n_groups = (int)bt->groups.size();
     if (branches) *branches = bt->branches;
     if (tiles_per_cta) *tiles_per_cta = bt->tiles_per_cta;
     if (proj_variant) *proj_variant = bt->proj_variant;

@@ -232,6 +232,7 @@ bool proj_tma_applies(const sp_basis *b, const void *frames);
 struct TunedShape {
     int branches, tiles_per_cta, proj_variant;
     float ms;
+    int grouped;   // 1: the plan localises groups of streams that share a basis
 };
 bool tune_cache_enabled();
 int tune_cache_get(const std::string &key, TunedShape *out, bool *found);

@@ -6,7 +6,7 @@
 //     "format": "svdphat-tune-cache",
 //     "version": 1,
 //     "plans": {
-//       "<key>": {"branches": 32, "tiles_per_cta": 1, "proj_variant": 0, "ms": 8.1727},
+//       "<key>": {"branches": 32, "tiles_per_cta": 1, "proj_variant": 0, "grouped": 1, "ms": 8.17},
 //       ...
 //     }
 //   }
@@ -102,11 +102,12 @@ int load(const std::string &path, std::map<std::string, TunedShape> *out) {
         if (o1 == std::string::npos) return bad();
         const std::string obj = s.substr(i, o1 - i + 1);
         i = o1 + 1;
-        double br, tpc, pv, ms;
+        double br, tpc, pv, ms, gr = 0.0;
         if (!valid_key(key) || !field(obj, "branches", &br) || !field(obj, "tiles_per_cta", &tpc) ||
             !field(obj, "proj_variant", &pv) || !field(obj, "ms", &ms))
             return bad();
-        (*out)[key] = TunedShape{(int)br, (int)tpc, (int)pv, (float)ms};
+        field(obj, "grouped", &gr);   // optional (0 when absent)
+        (*out)[key] = TunedShape{(int)br, (int)tpc, (int)pv, (float)ms, (int)gr};
         skip_ws(s, i);
         if (i < s.size() && s[i] == ',') ++i;
     }
@@ -120,9 +121,11 @@ int save(const std::string &path, const std::map<std::string, TunedShape> &m) {
     std::fprintf(f, "{\n  \"format\": \"svdphat-tune-cache\",\n  \"version\": 1,\n  \"plans\": {");
     bool first = true;
     for (const auto &kv : m) {
-        std::fprintf(f, "%s\n    \"%s\": {\"branches\": %d, \"tiles_per_cta\": %d, \"proj_variant\": %d, \"ms\": %.6g}",
+        std::fprintf(f,
+                     "%s\n    \"%s\": {\"branches\": %d, \"tiles_per_cta\": %d, \"proj_variant\": %d, "
+                     "\"grouped\": %d, \"ms\": %.6g}",
                      first ? "" : ",", kv.first.c_str(), kv.second.branches, kv.second.tiles_per_cta,
-                     kv.second.proj_variant, (double)kv.second.ms);
+                     kv.second.proj_variant, kv.second.grouped, (double)kv.second.ms);
         first = false;
     }
     std::fprintf(f, "\n  }\n}\n");
@@ -162,7 +165,7 @@ int tune_cache_put(const std::string &key, const TunedShape &v) {
     if (g_path.empty()) return SP_OK;
     SP_CHECK(valid_key(key), SP_EINVAL, "tune cache: bad key");
     SP_CHECK(v.branches >= 1 && (v.tiles_per_cta == 1 || v.tiles_per_cta == 2 || v.tiles_per_cta == 4) &&
-                 (v.proj_variant == 0 || v.proj_variant == 1) && v.ms >= 0.f,
+                 (v.proj_variant == 0 || v.proj_variant == 1) && (v.grouped == 0 || v.grouped == 1) && v.ms >= 0.f,
              SP_EINVAL, "tune cache: bad shape");
     std::map<std::string, TunedShape> m;
     SP_TRY(load(g_path, &m));   // a file that does not parse is left alone
@@ -182,9 +185,10 @@ int sp_set_tune_cache(const char *path) {
     return SP_OK;
 }
 
-int sp_tune_cache_get(const char *key, int *branches, int *tiles_per_cta, int *proj_variant, float *ms, int *found) {
+int sp_tune_cache_get(const char *key, int *branches, int *tiles_per_cta, int *proj_variant, float *ms, int *grouped,
+                      int *found) {
     SP_CHECK(key && found, SP_EINVAL, "sp_tune_cache_get: null pointer");
-    TunedShape v{0, 0, 0, 0.f};
+    TunedShape v{0, 0, 0, 0.f, 0};
     bool f = false;
     SP_TRY(tune_cache_get(key, &v, &f));
     *found = f ? 1 : 0;
@@ -193,13 +197,14 @@ int sp_tune_cache_get(const char *key, int *branches, int *tiles_per_cta, int *p
         if (tiles_per_cta) *tiles_per_cta = v.tiles_per_cta;
         if (proj_variant) *proj_variant = v.proj_variant;
         if (ms) *ms = v.ms;
+        if (grouped) *grouped = v.grouped;
     }
     return SP_OK;
 }
 
-int sp_tune_cache_put(const char *key, int branches, int tiles_per_cta, int proj_variant, float ms) {
+int sp_tune_cache_put(const char *key, int branches, int tiles_per_cta, int proj_variant, float ms, int grouped) {
     SP_CHECK(key, SP_EINVAL, "sp_tune_cache_put: null key");
-    return tune_cache_put(key, TunedShape{branches, tiles_per_cta, proj_variant, ms});
+    return tune_cache_put(key, TunedShape{branches, tiles_per_cta, proj_variant, ms, grouped});
 }
 
 }  // extern "C"

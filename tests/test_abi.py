@@ -144,7 +144,7 @@ def test_batch_and_proposal_calls_reject_bad_arguments(lib):
     assert lib.sp_batch_create(1, None, None, None, 1, 1, None, None, None, 0, None, None) == api.SP_EINVAL
     assert lib.sp_batch_create(1, None, None, None, 1, 1, None, None, None, 0, None, ctypes.byref(out)) == api.SP_EINVAL
     assert lib.sp_batch_run(None, None) == api.SP_EINVAL
-    assert lib.sp_batch_info(None, None, None, None, None, None, None) == api.SP_EINVAL
+    assert lib.sp_batch_info(None, None, None, None, None, None, None, None, None) == api.SP_EINVAL
     lib.sp_batch_destroy(None)
     assert lib.sp_proposal_create(None, None, 642, 256, 256, 0, ctypes.byref(out)) == api.SP_EINVAL
     assert lib.sp_proposal_create(None, None, 642, 256, 256, 0, None) == api.SP_EINVAL

@@ -173,7 +173,7 @@ def test_autotuned_plan_is_stored_and_reused(tmp_path):
         b2 = sp.Batch(bases, frames, "svd_exhaustive", "fp16", autotune=True, tune_kernels=True)
         i2 = b2.info()
         assert i2["from_cache"]
-        assert all(i2[k] == i1[k] for k in ("branches", "tiles_per_cta", "proj_variant"))
+        assert all(i2[k] == i1[k] for k in ("branches", "tiles_per_cta", "proj_variant", "grouped"))
         b1.run()
         b2.run()
         torch.cuda.synchronize()
@@ -195,3 +195,44 @@ def test_autotuned_plan_is_stored_and_reused(tmp_path):
         assert not b4.info()["from_cache"] and b4.info()["proj_variant"] == 0
     finally:
         sp.set_tune_cache(None)
+
+
+def _shared_basis_streams():
+    """Nine streams cut from the first three streams' frames (three slices each, so three per
+    basis: the plan forms three groups), plus one 8-byte-offset copy that stays alone."""
+    wls, bases, frames = _streams()
+    sb, sf = [], []
+    for i in range(3):
+        f = frames[i]
+        T = f.shape[0]
+        for a, z in [(0, T // 3), (T // 3, T // 2), (T // 2, T)]:
+            sb.append(bases[i])
+            sf.append(f[a:z].clone())
+    sb.append(bases[0])
+    sf.append(_offset_copy(frames[0][:40]))
+    return sb, sf
+
+
+@pytest.mark.parametrize("mode,prec,autotune", [("svd_exhaustive", "fp16", False), ("svd_exhaustive", "fp16", True),
+                                                ("svd_exhaustive", "fp32", False), ("svd_kdtree", "fp16", False)])
+def test_grouped_plan_equals_per_stream_localize(mode, prec, autotune):
+    """Streams that share a basis are copied into one buffer and localised by one call; each
+    stream's idx, score and proj are bit-identical to its own sp_localize call (the unaligned
+    stream runs alone, as sp_localize runs it on the register-fed kernel)."""
+    sb, sf = _shared_basis_streams()
+    bt = sp.Batch(sb, sf, mode, prec, autotune=autotune, group=not autotune)
+    info = bt.info()
+    assert info["n_groups"] == 3
+    if not autotune:
+        assert info["grouped"]
+    for f in bt.idx:
+        f.fill_(-7)
+    bt.run()
+    torch.cuda.synchronize()
+    sp.check_status()
+    for i, (b, f) in enumerate(zip(sb, sf)):
+        ref_prec = "fp32" if 2 * b.K > 288 or b.steering.M > 16 else prec
+        idx, score, proj = sp.localize(b, f, mode, ref_prec)
+        assert torch.equal(bt.idx[i], idx), i
+        assert torch.equal(bt.score[i], score), i
+        assert torch.equal(bt.proj[i], proj), i
